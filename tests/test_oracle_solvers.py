@@ -1,0 +1,96 @@
+"""Pins of the oracle's solvers (CPU only).
+
+  * MG (Algorithm 1) and PCG (Algorithm PCG) reach the dense-LU solution on
+    grids of at most 4 x 4 x 8 cells (box) and the n = 2, 4 cubed sphere;
+  * the V-cycle with zero initial guess is a linear map of the right-hand side;
+  * PCG's recursively updated residual equals the true b - A u;
+  * the tensor-product multigrid converges with a factor that does not drift
+    with n_z or lambda (Sec. 4.1.3, Boerm & Hiptmair; Table 6's finding that the
+    iteration count is independent of lambda^2), and the iteration count to a
+    1e-5 reduction does not grow with the horizontal resolution (Table 3).
+"""
+import numpy as np
+import pytest
+
+from paper_1307_2036_gb300 import inputs
+
+SMALL = [(0, 4, 8, False, 2), (0, 4, 8, True, 2), (1, 2, 8, True, 1), (1, 4, 8, False, 2)]
+
+
+@pytest.mark.parametrize("kind,n,nz,graded,cmin", SMALL)
+def test_solvers_match_dense_lu(oracle_mod, kind, n, nz, graded, cmin):
+    g = oracle_mod.Grid(kind, n, nz, inputs.radial_levels(nz, graded=graded), 0.05, 1.0,
+                        coarsest_min=cmin)
+    b = g.volumes() * inputs.uniform_pm1(g.shape(), member=7)
+    ref = np.linalg.solve(g.dense(), b.reshape(-1))
+    # 1e-11 is just above the attainable FP64 residual here (the dense LU
+    # solution itself leaves ~4e-12: the vertical coupling is ~1e5 x the mass).
+    u, it, hist = g.mg_solve(b, rtol=1e-11, maxit=100)
+    assert hist[-1] <= 1e-11
+    assert np.linalg.norm(u.reshape(-1) - ref) <= 1e-10 * np.linalg.norm(ref)
+    N = b.size
+    u2, it2, hist2 = g.pcg_solve(b, rtol=1e-11, maxit=N)
+    assert it2 <= N and hist2[-1] < 1e-11
+    assert np.linalg.norm(u2.reshape(-1) - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_vcycle_is_linear(oracle_mod):
+    g = oracle_mod.Grid(1, 8, 8, inputs.radial_levels(8, graded=True), 0.01, 1.0)
+    b1 = g.volumes() * inputs.uniform_pm1(g.shape(), member=1)
+    b2 = g.volumes() * inputs.gaussian(g.shape(), member=2)
+    z = np.zeros(g.shape())
+    v12 = g.vcycle(b1 + 3.0 * b2, z)
+    v1, v2 = g.vcycle(b1, z), g.vcycle(b2, z)
+    assert np.linalg.norm(v12 - (v1 + 3.0 * v2)) <= 1e-13 * np.linalg.norm(v12)
+
+
+def test_pcg_recursive_residual_is_true_residual(oracle_mod):
+    g = oracle_mod.Grid(0, 16, 16, inputs.radial_levels(16, graded=True), 0.01, 1.0)
+    b = g.volumes() * inputs.uniform_pm1(g.shape())
+    u, it, hist = g.pcg_solve(b, rtol=1e-9, maxit=500)
+    true_rel = np.linalg.norm(g.residual(b, u)) / np.linalg.norm(b)
+    assert abs(true_rel - hist[-1]) <= 1e-3 * hist[-1] + 1e-14
+
+
+def rate(g, rtol=1e-8):
+    b = g.volumes() * inputs.uniform_pm1(g.shape())
+    _, it, hist = g.mg_solve(b, rtol=rtol, maxit=60)
+    return hist[-1] ** (1.0 / it), it
+
+
+def test_mg_factor_robust_in_nz_and_lambda(oracle_mod):
+    rates = {}
+    for nz in (8, 16, 32, 64):
+        for lam in (0.1, 1.0, 10.0):
+            g = oracle_mod.Grid(0, 32, nz, inputs.radial_levels(nz), 0.01, lam * lam)
+            rates[(nz, lam)] = rate(g)[0]
+    vals = np.array(list(rates.values()))
+    assert vals.max() <= 0.3, rates
+    assert vals.max() - vals.min() <= 0.05, rates
+
+
+def test_mg_iterations_do_not_grow_with_n(oracle_mod):
+    """Weak scaling as in Sec. 5.1: the time step shrinks with the grid spacing,
+    so omega^2 n^2 (the horizontal coupling C_horiz, Eq. Choriz) stays fixed.
+    The number of V-cycles to a 1e-5 reduction then stays fixed (Table 3)."""
+    its = []
+    for n in (32, 64, 128):
+        g = oracle_mod.Grid(1, n, 16, inputs.radial_levels(16, graded=True),
+                            0.04 * (32.0 / n) ** 2, 1.0)
+        b = g.volumes() * inputs.uniform_pm1(g.shape())
+        _, it, _ = g.mg_solve(b, rtol=1e-5, maxit=60)
+        its.append(it)
+    assert max(its) - min(its) <= 1 and max(its) <= 8, its
+
+
+def test_mg_beats_cg_and_cg_grows_with_omega(oracle_mod):
+    """Table 6: MG is nearly unaffected by a 100x larger omega^2 while CG with
+    line relaxation needs many more iterations."""
+    out = {}
+    for f in (1.0, 100.0):
+        g = oracle_mod.Grid(0, 32, 16, inputs.radial_levels(16, graded=True), 1e-3 * f, 1.0)
+        b = g.volumes() * inputs.uniform_pm1(g.shape())
+        out[f] = (g.mg_solve(b, rtol=1e-5, maxit=60)[1], g.pcg_solve(b, rtol=1e-5, maxit=2000)[1])
+    assert out[100.0][0] <= out[1.0][0] + 3
+    assert out[100.0][1] >= 3 * out[1.0][1]
+    assert out[100.0][0] < out[100.0][1]
