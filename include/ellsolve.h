@@ -1,0 +1,185 @@
+/*
+ * ellsolve -- GB300 (sm_103a) solver for the elliptic model equation of
+ * Mueller & Scheichl, "Massively parallel solvers for elliptic PDEs in
+ * Numerical Weather- and Climate Prediction" (arXiv:1307.2036):
+ *
+ *     -omega^2 (Laplace_2d u + lambda^2 r^-2 d/dr (r^2 du/dr)) + u = f     (Eq. ModelEquation)
+ *
+ * on the shell 1 <= r <= 1 + H over a doubly periodic box or the cubed sphere
+ * (Eqs. x1x2_1, x1x2_2), homogeneous Neumann at the bottom and top (Sec. 2),
+ * discretised with cell-centred finite volumes and a 7-point stencil
+ * (Sec. 2.1).  Solvers: the tensor-product geometric multigrid V-cycle
+ * (Algorithm 1; horizontal-only coarsening, vertical line relaxation,
+ * Sec. 4.1.3 and 5.2.1) and CG preconditioned by vertical line relaxation
+ * (Algorithm PCG, Sec. 5.2.2).
+ *
+ * Conventions for every call below:
+ *  - Vectors are device buffers of doubles in the layout [nz][P][n][n]:
+ *    element (k, p, j, i) at ((k * P + p) * n + j) * n + i, P = 1 (box) or 6
+ *    (sphere).  Panel p of the sphere is the cube face with outward normal
+ *    N_p, its index i runs along A_p and j along B_p, where
+ *      p  N_p        A_p        B_p
+ *      0  (+1,0,0)   (0,+1,0)   (0,0,+1)
+ *      1  (0,+1,0)   (-1,0,0)   (0,0,+1)
+ *      2  (-1,0,0)   (0,-1,0)   (0,0,+1)
+ *      3  (0,-1,0)   (+1,0,0)   (0,0,+1)
+ *      4  (0,0,+1)   (0,+1,0)   (-1,0,0)
+ *      5  (0,0,-1)   (0,+1,0)   (+1,0,0)
+ *    and a point of the panel is N_p + xi A_p + eta B_p projected to the sphere.
+ *  - Right-hand sides are the pointwise f of Eq. ModelEquation; the library
+ *    forms the volume-integrated b = A_P V_k f.  ellsolve_apply returns the
+ *    matrix-vector product y = A x of the finite-volume matrix (volume
+ *    integrated).  Relative residuals are ||b - A u||_2 / ||b||_2.
+ *  - Buffers are owned by the caller; the library never frees them and only
+ *    reads/writes them on the handle's CUDA stream, in stream order.
+ *  - Calls return a status; none aborts.  On an error the thread-local
+ *    message of ellsolve_last_error() says what failed.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef ELLSOLVE_H
+#define ELLSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ellsolve_s *ellsolve_t;
+typedef struct ellsolve_server_s *ellsolve_server_t;
+
+typedef enum {
+    ELLSOLVE_OK = 0,
+    ELLSOLVE_NOT_CONVERGED = 1, /* maxit reached, or the residual stagnated above rtol */
+    ELLSOLVE_PENDING = 2,       /* ellsolve_poll: not finished within the timeout */
+    ELLSOLVE_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad option) */
+    ELLSOLVE_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    ELLSOLVE_ERR_NOMEM = -3,    /* device memory allocation failed */
+    ELLSOLVE_ERR_NONFINITE = -4,/* a residual norm became NaN or Inf */
+    ELLSOLVE_ERR_CAPACITY = -5  /* request larger than the server's HBM budget or slots */
+} ellsolve_status;
+
+typedef struct {
+    int kind;        /* 0: doubly periodic box (P = 1), 1: cubed sphere (P = 6) */
+    int n;           /* cells per panel side (>= 1) */
+    int nz;          /* vertical levels (>= 1) */
+    double box_side; /* box only: side length (2 pi in the configs) */
+    int mapping;     /* sphere only: 0 equiangular, 1 equidistant gnomonic (Eq. x1x2_2) */
+} ellsolve_grid;
+
+typedef struct {
+    int precision;    /* 0: FP64 throughout; 1: FP32 V-cycles inside FP64 iterative refinement */
+    int solver;       /* 0: multigrid V-cycles (Algorithm 1); 1: PCG (Algorithm PCG) */
+    int nu_pre;       /* pre-smoothing line-Jacobi sweeps (2) */
+    int nu_post;      /* post-smoothing sweeps (2) */
+    int nu_coarse;    /* sweeps on the coarsest level (2) */
+    double damping;   /* line-Jacobi damping rho (0.8); the coarsest level is undamped */
+    int coarsest_min; /* coarsen while n is even and n/2 >= coarsest_min (4) */
+    int max_levels;   /* cap on the number of levels, <= 0: no cap */
+    int prolong;      /* 0: bilinear (cell-centred), 1: piecewise constant */
+    int inner_cycles; /* precision 1: V-cycles per refinement step (1) */
+    int use_graph;    /* 1: replay the per-iteration work as a CUDA graph */
+} ellsolve_opts;
+
+typedef struct {
+    int iterations;      /* V-cycles (MG) or CG iterations done */
+    double rel_residual; /* final ||b - A u|| / ||b|| (FP64) */
+    double seconds;      /* wall time of the solve on the stream */
+} ellsolve_result;
+
+/* Fill *o with the defaults listed above. */
+void ellsolve_default_opts(ellsolve_opts *o);
+
+/* Build the grid hierarchy and device workspace for one problem.
+ *  grid     : box or cubed sphere (copied).
+ *  omega2   : omega^2 of Eq. ModelEquation (> 0).
+ *  lambda2  : lambda^2 (> 0).
+ *  r_levels : host array of nz+1 radii, strictly increasing (copied); Eq.
+ *             VerticalGrading gives r_k = 1 + H (k/nz)^2.
+ *  opts     : solver options (copied; NULL = defaults).
+ *  stream   : cudaStream_t for every later call on the handle (NULL = legacy default).
+ *  out      : receives the handle.
+ * Errors: ELLSOLVE_ERR_ARG, ELLSOLVE_ERR_NOMEM, ELLSOLVE_ERR_CUDA. */
+ellsolve_status ellsolve_create(const ellsolve_grid *grid, double omega2, double lambda2,
+                                const double *r_levels, const ellsolve_opts *opts,
+                                void *stream, ellsolve_t *out);
+void ellsolve_destroy(ellsolve_t h);
+
+/* Sizes: unknowns on the finest level, and the hierarchy depth. */
+size_t ellsolve_size(ellsolve_t h);
+int ellsolve_num_levels(ellsolve_t h);
+
+/* y = A x on the finest level (Sec. 2.1 stencil), FP64 device buffers. */
+ellsolve_status ellsolve_apply(ellsolve_t h, const void *x_dev, void *y_dev);
+
+/* One multigrid V-cycle (Algorithm 1) in place on u_dev for the pointwise
+ * right-hand side f_dev.  precision 1: one refinement step (FP64 residual, FP32
+ * V-cycle on it, FP64 update). */
+ellsolve_status ellsolve_vcycle(ellsolve_t h, const void *f_dev, void *u_dev);
+
+/* Solve A x = b (b = volume-integrated f) from x = 0 until the relative
+ * residual is <= rtol, maxit iterations pass, or the residual stops falling
+ * (the attainable FP64 residual is about eps ||A|| ||x|| / ||b||).
+ * Returns OK, NOT_CONVERGED (result and x still filled), or an error. */
+ellsolve_status ellsolve_solve(ellsolve_t h, const void *rhs_dev, void *x_dev, double rtol,
+                               int maxit, ellsolve_result *res);
+
+/* Solve several independent problems in one pass: every multigrid kernel is
+ * launched once per level over all members (count handles, all created with
+ * precision 1 and solver 0, on the same stream as handles[0]).  rhs/x: arrays
+ * of count device pointers.  res: count results.  Returns the worst status. */
+ellsolve_status ellsolve_solve_batch(ellsolve_t *handles, int count, const void *const *rhs_dev,
+                                     void *const *x_dev, double rtol, int maxit,
+                                     ellsolve_result *res);
+
+/* ---- per-level operations on the handle's hierarchy (kernel-level access) ----
+ * Vectors here are volume-integrated right-hand sides b and iterates u of level
+ * `level` (0 finest) in the same [nz][P][n][n] layout; fp32 selects float
+ * buffers and the FP32 kernels, otherwise double. */
+ellsolve_status ellsolve_level_shape(ellsolve_t h, int level, int *n, size_t *ncol);
+/* y = A_level x */
+ellsolve_status ellsolve_level_apply(ellsolve_t h, int level, int fp32, const void *x, void *y);
+/* r = b - A_level u */
+ellsolve_status ellsolve_level_residual(ellsolve_t h, int level, int fp32, const void *b,
+                                        const void *u, void *r);
+/* nsweeps damped block-Jacobi vertical line relaxation sweeps (Sec. 3.2,
+ * Algorithm Thomas per column), u <- u + rho Dtilde^{-1}(b - A u), in place. */
+ellsolve_status ellsolve_level_smooth(ellsolve_t h, int level, int fp32, const void *b, void *u,
+                                      int nsweeps, double rho);
+/* b_c = R (b - A u) on level+1: residual summed over the 2 x 2 children (Sec. 5.2.1). */
+ellsolve_status ellsolve_level_restrict_residual(ellsolve_t h, int level, int fp32,
+                                                 const void *b, const void *u, void *b_c);
+/* u += P u_c from level+1 (bilinear or constant per opts.prolong). */
+ellsolve_status ellsolve_level_prolong_add(ellsolve_t h, int level, int fp32, const void *u_c,
+                                           void *u);
+
+/* ---- profiling: CUDA-event time of the finest-level smoother launches ---- */
+ellsolve_status ellsolve_profile_enable(ellsolve_t h, int enable);
+ellsolve_status ellsolve_profile_read(ellsolve_t h, double *smoother_ms_total, int *launches,
+                                      double *bytes_per_launch);
+/* number of kernel launches the library issued on this handle so far */
+uint64_t ellsolve_launch_count(ellsolve_t h);
+
+/* ---- serving: continuous batching of independent solves ----
+ * A server owns one CUDA stream's worth of work; submitted requests are admitted
+ * while their device footprint fits hbm_budget_bytes and a slot is free, and
+ * all admitted requests advance together (one batched launch per level). */
+ellsolve_status ellsolve_server_create(size_t hbm_budget_bytes, int max_slots, void *stream,
+                                       ellsolve_server_t *out);
+/* Copies grid, parameters and r_levels; borrows rhs_dev and x_dev until the
+ * request's poll returns OK, NOT_CONVERGED or an error. */
+ellsolve_status ellsolve_submit(ellsolve_server_t s, const ellsolve_grid *grid, double omega2,
+                                double lambda2, const double *r_levels, const void *rhs_dev,
+                                void *x_dev, double rtol, int maxit, uint64_t *ticket);
+/* Wait up to timeout_us (0: do not wait, < 0: forever) for the request. */
+ellsolve_status ellsolve_poll(ellsolve_server_t s, uint64_t ticket, int timeout_us,
+                              ellsolve_result *res);
+void ellsolve_server_destroy(ellsolve_server_t s);
+
+const char *ellsolve_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

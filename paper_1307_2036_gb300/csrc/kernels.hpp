@@ -1,0 +1,80 @@
+// Host-callable launchers of the ellsolve kernels (defined in kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ells {
+
+// Line smoother: one damped block-Jacobi sweep on every item of `items`
+// (nitems blocks of kBlk columns).  max_nz: largest nz among the items'
+// descriptors (sizes the shared-memory Thomas scratch).
+template <typename T>
+cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems, T rho,
+                          int max_nz);
+
+// mode 0: aux = A u[in]; mode 1: aux = b - A u[in]; mode 2: only the partial
+// sums of (b - A u[in])^2 into partials[item] (FP64).
+template <typename T>
+cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems, int mode,
+                         double *partials);
+
+// b of descriptor lv+1 = 2x2 sums of (b - A u[in]) on descriptor lv.  Items
+// run over the coarse columns.
+template <typename T>
+cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems);
+
+// u[out] of descriptor lv += P u[in] of descriptor lv+1 (items: fine columns).
+// mode 0 bilinear, 1 constant.
+template <typename T>
+cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
+                               int mode);
+
+// Iterative-refinement outer step, per member m (items' lv = member index):
+//   r = A_P V_k f - A x   in FP64, f = L64[m].b (pointwise), x = L64[m].u[0],
+//   L32[m].b = float(r * scale[m]), partials[item] = sum of r^2.
+cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
+                               const Item *items, int nitems, const double *scale,
+                               double *partials);
+// x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with active[m] != 0
+cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
+                             const Item *items, int nitems, const double *scale,
+                             const int *active);
+
+// b = A_P V_k f on every item (FP64 or FP32 output), partial sums of b^2.
+template <typename T>
+cudaError_t launch_form_rhs(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
+                            const double *f, T *b, double *partials);
+
+// Deterministic finishing of block partials: out[m] = sum of partials[first[m]
+// .. first[m+1]) in a fixed order, for m < nmembers.  op 0: plain sum; op 1:
+// sqrt of the sum; op 2: as 1 and also scale_out[m] = sqrt(count)/norm when
+// scale_out != null.
+cudaError_t launch_finalize(cudaStream_t s, const double *partials, const int *first, int nmembers,
+                            double *out, int op, double *scale_out, const double *counts);
+
+// ---- preconditioned CG (FP64, finest level of one problem) ----
+// q = A p and partials of p.q
+cudaError_t launch_cg_apply_dot(cudaStream_t s, const Lv<double> *L, const Item *items, int nitems,
+                                const double *p, double *q, double *partials);
+// alpha = sc[KAPPA]/pq; u += alpha p; r -= alpha q; partials of r.r
+cudaError_t launch_cg_update(cudaStream_t s, const Lv<double> *L, const Item *items, int nitems,
+                             double *u, double *r, const double *p, const double *q,
+                             const double *scalars, double *partials);
+// z = Dtilde^{-1} r (scratch holds the Thomas coefficients) and partials of r.z
+cudaError_t launch_cg_precond_dot(cudaStream_t s, const Lv<double> *L, const Item *items,
+                                  int nitems, const double *r, double *z, double *scratch,
+                                  double *partials);
+// p = z + beta p, beta = scalars[...] ; n elements
+cudaError_t launch_cg_xpay(cudaStream_t s, const double *z, double *p, const double *scalars,
+                           size_t n);
+// scalar bookkeeping of Algorithm PCG on the device
+//   op 0: scalars[KAPPA] = rz, scalars[R0] = sqrt(rr)      (set-up)
+//   op 1: scalars[ALPHA] = scalars[KAPPA] / pq
+//   op 2: scalars[BETA] = rz / scalars[KAPPA]; scalars[KAPPA] = rz
+cudaError_t launch_cg_scalars(cudaStream_t s, double *scalars, const double *sums, int op);
+
+enum CgSlot { kKappa = 0, kAlpha = 1, kBeta = 2, kR0 = 3 };
+
+}  // namespace ells

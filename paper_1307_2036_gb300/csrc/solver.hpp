@@ -1,0 +1,151 @@
+// Internal host-side types of the ellsolve driver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ellsolve.h"
+
+namespace ells {
+
+struct Error : std::runtime_error {
+    ellsolve_status status;
+    Error(ellsolve_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+void check_cuda(cudaError_t e, const char *what);
+void set_last_error(const std::string &m);
+
+// Owning device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            reset();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { reset(); }
+    void alloc(size_t b);
+    void reset();
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Device storage of one multigrid level of one problem.
+struct LevelStore {
+    int n = 0, ncol = 0;
+    DevBuf area64, tr64, area32, tr32, nbr, pst;
+    DevBuf u64[2], b64, aux64;
+    DevBuf u32[2], b32, aux32;
+};
+
+// One launch of a V-cycle program.
+struct Op {
+    enum Kind { kSmooth, kRestrict, kProlong, kMemset } kind = kSmooth;
+    int off = 0, n = 0;       // range in the plan's item array
+    double rho = 1.0;         // smoother damping
+    int max_nz = 0;           // largest nz among the items
+    bool finest = false;      // smooths a finest level (profiled)
+    int member = 0, level = 0, buf = 0;  // kMemset target
+};
+
+struct Program {
+    std::vector<Op> ops;
+    std::vector<int> fine_cur_out;  // finest-level buffer per member after the cycle
+    int update_off = 0, update_n = 0;
+};
+
+struct Problem;
+
+// The launch program of a set of problems ("members") solved together: every
+// kernel of the V-cycle is one launch over the items of all members.
+struct Plan {
+    std::vector<Problem *> mem;
+    int precision = 1;
+    std::vector<int> base;  // first descriptor of each member
+    int maxlev = 0, maxnz = 0;
+    DevBuf desc64, desc32;  // level descriptors, member-major
+    DevBuf outer64, fine32; // finest-level descriptors per member for the refinement
+    std::vector<Lv<double>> stage64;
+    std::vector<Lv<float>> stage32;
+    std::vector<double> stage_scales;
+    std::vector<Item> items;
+    DevBuf ditems;
+    bool items_dirty = true;
+    std::map<std::string, Program> programs;
+    int outer_off = 0, outer_n = 0;   // finest columns, lv = member
+    int norm_off[2] = {0, 0}, norm_n = 0;  // finest columns, lv = descriptor, u[0] / u[1]
+    std::vector<int> outer_first;     // per-member ranges of outer items
+    DevBuf dfirst, partials, norms, scales, counts, active;
+    std::vector<int> stage_active;
+    std::vector<double> host_norms;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_launches = 0;
+
+    ~Plan();
+    void build(const std::vector<Problem *> &members, int prec);
+    const Program &program(bool fine_zero, const std::vector<int> &fine_cur);
+    void sync_items();
+    void drop_graph();
+};
+
+struct Problem {
+    ellsolve_grid grid{};
+    ellsolve_opts opts{};
+    double omega2 = 0, lambda2 = 0;
+    std::vector<double> r;
+    int nz = 0, P = 1, nlev = 0;
+    size_t N = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<LevelStore> lev;
+    DevBuf V64, g64, V32, g32;
+    std::vector<Lv<double>> h64;
+    std::vector<Lv<float>> h32;
+    int fine_cur = 0;
+    DevBuf cg[4], cg_scal;
+    std::unique_ptr<Plan> plan, batch_plan;
+    double *pinned = nullptr;
+    uint64_t launches = 0;
+    bool capturing = false;
+    // CUDA-event timing of the finest-level smoother launches
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free, ev_graph;
+    int ev_next = 0, ev_graph_used = 0;
+    double prof_ms = 0.0;
+    long prof_count = 0;
+
+    ~Problem();
+    void build(const ellsolve_grid &g, double w2, double l2, const double *r_levels,
+               const ellsolve_opts &o, cudaStream_t s);
+    Plan &single_plan();
+    size_t footprint_bytes() const;
+    void prof_mark_begin(cudaStream_t s);
+    void prof_mark_end(cudaStream_t s);
+    void prof_collect(bool graph_replayed);
+};
+
+ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
+                         const std::vector<double *> &x, double rtol, int maxit,
+                         std::vector<ellsolve_result> &res);
+
+}  // namespace ells

@@ -1,0 +1,50 @@
+"""Helpers shared by the GPU tests: paired oracle / library problems on the
+same seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_1307_2036_gb300 import inputs
+
+
+def require_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    # on a GPU machine the library must be present: importing fails loudly otherwise
+    from paper_1307_2036_gb300 import ellsolve  # noqa: F401
+    return torch
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+class Pair:
+    """An oracle grid and a library solver for the same problem."""
+
+    def __init__(self, oracle_mod, kind, n, nz, omega2=0.01, lambda2=1.0, graded=False, mapping=0,
+                 precision=0, solver=0, coarsest_min=4, **opts):
+        import torch
+        from paper_1307_2036_gb300 import ellsolve
+        self.torch = torch
+        self.r = inputs.radial_levels(nz, graded=graded)
+        self.og = oracle_mod.Grid(kind, n, nz, self.r, omega2, lambda2, mapping=mapping,
+                                  coarsest_min=coarsest_min, max_levels=opts.get("max_levels", 0))
+        self.sv = ellsolve.Solver(kind, n, nz, self.r, omega2, lambda2, mapping=mapping,
+                                  precision=precision, solver=solver, coarsest_min=coarsest_min,
+                                  **opts)
+        assert self.sv.nlevels == self.og.nlevels
+
+    def dev(self, a, fp32=False):
+        t = self.torch.tensor(np.ascontiguousarray(a), dtype=self.torch.float64, device="cuda")
+        return t.float().contiguous() if fp32 else t
+
+    def host(self, t):
+        self.torch.cuda.synchronize()
+        return t.double().cpu().numpy()
+
+    def empty(self, level=0, fp32=False):
+        dt = self.torch.float32 if fp32 else self.torch.float64
+        return self.torch.zeros(self.og.shape(level), dtype=dt, device="cuda")

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA library against the FP64 oracle, element by element, on
+the same seeded inputs, through the C ABI (ctypes binding).
+
+Tolerances:
+  FP64 kernels         relative L2 1e-12 per kernel; 1e-10 after a fixed number
+                       of V-cycles / CG iterations (the stated FP64 bar).
+  FP32 kernels         relative L2 1e-5 against the FP64 oracle on inputs that
+                       are exactly representable in FP32 (rounding of one pass).
+  mixed-precision      relative L2 1e-9 against the oracle's converged solution.
+Sizes span several 128-column tiles with a ragged last tile.
+"""
+import numpy as np
+import pytest
+
+from paper_1307_2036_gb300 import inputs
+from gpu_util import Pair, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+# kind, n, nz, graded, mapping, omega2, lambda2
+CASES = [
+    (0, 24, 16, False, 0, 0.01, 1.0),    # box, 576 columns, 3 levels
+    (0, 20, 12, True, 0, 0.1, 25.0),     # box, graded, strong coupling
+    (1, 12, 16, True, 0, 0.01, 1.0),     # equiangular sphere, 864 columns
+    (1, 16, 8, False, 1, 0.05, 0.25),    # equidistant sphere, 3 levels
+    (1, 8, 128, True, 0, 0.01, 1.0),     # the 128-level graded column of the sphere configs
+]
+IDS = ["box24", "box20g", "sph12", "sph16e", "sph8z128"]
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return require_gpu()
+
+
+def make(oracle_mod, case, precision=0, **kw):
+    kind, n, nz, graded, mapping, w2, l2 = case
+    return Pair(oracle_mod, kind, n, nz, omega2=w2, lambda2=l2, graded=graded, mapping=mapping,
+                precision=precision, **kw)
+
+
+def rand(shape, member, scale=1.0):
+    return scale * inputs.uniform_pm1(shape, member=member)
+
+
+def f32exact(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_apply_and_residual_fp64(torch_mod, oracle_mod, case):
+    p = make(oracle_mod, case)
+    u = rand(p.og.shape(), 1)
+    b = p.og.volumes() * rand(p.og.shape(), 2)
+    y = p.empty()
+    p.sv.apply(p.dev(u), y)
+    assert rel_l2(p.host(y), p.og.apply(u)) <= 1e-13
+    for lev in range(p.og.nlevels):
+        ul = rand(p.og.shape(lev), 3 + lev)
+        bl = p.og.volumes(lev) * rand(p.og.shape(lev), 10 + lev)
+        r = p.empty(lev)
+        p.sv.level_residual(lev, p.dev(bl), p.dev(ul), r)
+        assert rel_l2(p.host(r), p.og.residual(bl, ul, lev)) <= 1e-13, lev
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+@pytest.mark.parametrize("nsweeps", [1, 3])
+def test_line_smoother_fp64(torch_mod, oracle_mod, case, nsweeps):
+    p = make(oracle_mod, case)
+    for lev in range(p.og.nlevels):
+        u = rand(p.og.shape(lev), 20 + lev)
+        b = p.og.volumes(lev) * rand(p.og.shape(lev), 30 + lev)
+        ud = p.dev(u)
+        p.sv.level_smooth(lev, p.dev(b), ud, nsweeps=nsweeps, rho=0.8)
+        ref = p.og.smooth(b, u, nsweeps=nsweeps, rho=0.8, lev=lev)
+        assert rel_l2(p.host(ud), ref) <= 1e-12, lev
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_transfers_fp64(torch_mod, oracle_mod, case, mode):
+    p = make(oracle_mod, case, prolong=mode)
+    for lev in range(p.og.nlevels - 1):
+        u = rand(p.og.shape(lev), 40 + lev)
+        b = p.og.volumes(lev) * rand(p.og.shape(lev), 50 + lev)
+        bc = p.empty(lev + 1)
+        p.sv.level_restrict_residual(lev, p.dev(b), p.dev(u), bc)
+        ref = p.og.restrict(p.og.residual(b, u, lev), lev)
+        assert rel_l2(p.host(bc), ref) <= 1e-13
+        uc = rand(p.og.shape(lev + 1), 60 + lev)
+        uf = p.dev(u)
+        p.sv.level_prolong_add(lev, p.dev(uc), uf)
+        assert rel_l2(p.host(uf), p.og.prolong_add(uc, u, lev, mode=mode)) <= 1e-15
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_kernels_fp32(torch_mod, oracle_mod, case):
+    p = make(oracle_mod, case, precision=1)
+    for lev in range(p.og.nlevels):
+        u = f32exact(rand(p.og.shape(lev), 70 + lev))
+        b = f32exact(p.og.volumes(lev) * rand(p.og.shape(lev), 80 + lev))
+        r = p.empty(lev, fp32=True)
+        p.sv.level_residual(lev, p.dev(b, True), p.dev(u, True), r, fp32=True)
+        assert rel_l2(p.host(r), p.og.residual(b, u, lev)) <= 1e-5
+        ud = p.dev(u, True)
+        p.sv.level_smooth(lev, p.dev(b, True), ud, nsweeps=2, rho=0.8, fp32=True)
+        assert rel_l2(p.host(ud), p.og.smooth(b, u, 2, 0.8, lev)) <= 1e-5
+        if lev + 1 < p.og.nlevels:
+            bc = p.empty(lev + 1, fp32=True)
+            p.sv.level_restrict_residual(lev, p.dev(b, True), p.dev(u, True), bc, fp32=True)
+            ref = p.og.restrict(p.og.residual(b, u, lev), lev)
+            assert rel_l2(p.host(bc), ref) <= 1e-5
+            uc = f32exact(rand(p.og.shape(lev + 1), 90 + lev))
+            uf = p.dev(u, True)
+            p.sv.level_prolong_add(lev, p.dev(uc, True), uf, fp32=True)
+            assert rel_l2(p.host(uf), p.og.prolong_add(uc, u, lev)) <= 1e-6
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_vcycles_fp64_fixed_count(torch_mod, oracle_mod, case):
+    p = make(oracle_mod, case)
+    f = rand(p.og.shape(), 100)
+    b = p.og.volumes() * f
+    u_ref = p.og.zeros()
+    ud = p.empty()
+    fd = p.dev(f)
+    for _ in range(3):
+        p.sv.vcycle(fd, ud)
+        u_ref = p.og.vcycle(b, u_ref)
+    assert rel_l2(p.host(ud), u_ref) <= 1e-10
+    # the solve entry point with a fixed count (rtol 0): same iterate
+    x = p.empty()
+    st, res = p.sv.solve(fd, x, rtol=0.0, maxit=4)
+    u4, it, hist = p.og.mg_solve(b, rtol=0.0, maxit=4)
+    assert res.iterations == 4 and it == 4
+    assert rel_l2(p.host(x), u4) <= 1e-10
+    assert abs(res.rel_residual - hist[-1]) <= 1e-6 * hist[-1] + 1e-15
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_pcg_fp64_fixed_count(torch_mod, oracle_mod, case):
+    p = make(oracle_mod, case, solver=1)
+    f = rand(p.og.shape(), 110)
+    b = p.og.volumes() * f
+    x = p.empty()
+    st, res = p.sv.solve(p.dev(f), x, rtol=0.0, maxit=20)
+    u_ref, it, hist = p.og.pcg_solve(b, rtol=0.0, maxit=20)
+    assert res.iterations == 20 and it == 20
+    assert rel_l2(p.host(x), u_ref) <= 1e-10
+    assert abs(res.rel_residual - hist[-1]) <= 1e-6 * hist[-1]
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_mixed_precision_solution(torch_mod, oracle_mod, case):
+    """FP32 V-cycles inside FP64 refinement against the oracle's converged
+    FP64 multigrid solution: relative L2 <= 1e-9."""
+    p = make(oracle_mod, case, precision=1)
+    f = rand(p.og.shape(), 120)
+    b = p.og.volumes() * f
+    u_ref, it_ref, hist_ref = p.og.mg_solve(b, rtol=1e-13, maxit=80)
+    x = p.empty()
+    st, res = p.sv.solve(p.dev(f), x, rtol=1e-12, maxit=80)
+    err = rel_l2(p.host(x), u_ref)
+    print(f"mixed: {res.iterations} cycles, rel residual {res.rel_residual:.2e}, error {err:.2e}")
+    assert err <= 1e-9
+    assert res.rel_residual <= max(1e-11, 10 * hist_ref[-1])
+
+
+def test_manufactured_mode_closed_form(torch_mod, oracle_mod):
+    """Config-1 box with the Fourier(3,5) x cos(mode 2) right-hand side: the
+    mixed solve reproduces the closed-form discrete solution."""
+    import sys
+    sys.path.insert(0, __file__.rsplit("/", 1)[0])
+    from test_oracle_operator import fourier_exact
+    n, nz = 32, 32
+    p = Pair(oracle_mod, 0, n, nz, precision=1)
+    f = inputs.fourier_cos_mode(n, nz)
+    x = p.empty()
+    st, res = p.sv.solve(p.dev(f), x, rtol=1e-11, maxit=50)
+    exact = fourier_exact(n, nz, p.r, 0.01, 1.0)
+    assert rel_l2(p.host(x), exact) <= 1e-9
+
+
+def test_batch_equals_alone(torch_mod, oracle_mod):
+    """Members of a batch give bit-identical results to the same solves alone."""
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    specs = [(1, 8, 16, 0.01, 1.0), (0, 24, 12, 0.05, 4.0), (1, 12, 8, 0.002, 0.5)]
+    solvers, rhs = [], []
+    for m, (kind, n, nz, w2, l2) in enumerate(specs):
+        s = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=True), w2, l2, precision=1)
+        solvers.append(s)
+        rhs.append(torch.tensor(inputs.uniform_pm1(s.shape(), member=m), device="cuda"))
+    alone = []
+    for s, f in zip(solvers, rhs):
+        x = torch.zeros_like(f)
+        st, res = s.solve(f, x, rtol=1e-8, maxit=30)
+        alone.append((x.clone(), res.iterations))
+    xs = [torch.zeros_like(f) for f in rhs]
+    st, res = ellsolve.solve_batch(solvers, rhs, xs, rtol=1e-8, maxit=30)
+    for (xa, ita), xb, rb in zip(alone, xs, res):
+        assert ita == rb.iterations
+        assert torch.equal(xa, xb)
+        assert rb.rel_residual <= 1e-8
