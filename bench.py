@@ -1,0 +1,308 @@
+"""Benchmark of the GB300 ellsolve library on the cubed-sphere workload.
+
+Default workload (one GPU): equiangular cubed sphere 6 x 512 x 512 cells x 128
+quadratically graded levels on r in [1, 1.01] (201,326,592 unknowns),
+omega^2 = 0.01, lambda = 1, right-hand side N(0, 1) smoothed by three in-panel
+Jacobi sweeps; FP32 V-cycles (2/2 line-Jacobi sweeps, damping 0.8, coarsened to
+4 x 4 per panel) inside FP64 iterative refinement, each refinement step replayed
+as one CUDA graph.  One step = one solve from x = 0 to a 1e-5 relative residual
+reduction.  Metric: unknowns x V-cycles per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload sphere512|sphere128|box256]
+
+Under torchrun every rank solves its own instance of the workload (the solve
+itself is not split across GPUs); value = all ranks' unknowns x V-cycles / the
+slowest rank's time.  --impl reference times the FP64 CPU oracle instead, on a
+bounded sample of the same workload (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "unknowns*V-cycles/s"
+WORKLOADS = {
+    # name: (kind, n, nz, graded, omega2, lambda2, rhs, rtol)
+    "sphere512": (1, 512, 128, True, 0.01, 1.0, "smooth_gauss", 1e-5),
+    "sphere128": (1, 128, 128, True, 0.01, 1.0, "smooth_gauss", 1e-5),
+    "box256": (0, 256, 64, True, 0.01, 1.0, "uniform", 1e-5),
+}
+# bounded oracle sample for the CPU baseline: the same sphere at 1/16 of the columns
+ORACLE_SAMPLE = (1, 128, 128, True, 0.01, 1.0)
+
+
+def rhs_for(kind, n, nz, how, member=0):
+    from paper_1307_2036_gb300 import inputs
+    shape = (nz, 1 if kind == 0 else 6, n, n)
+    if how == "uniform":
+        return inputs.uniform_pm1(shape, member=member)
+    return inputs.smooth_per_panel(inputs.gaussian(shape, member=member), sweeps=3)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(sample, vcycles):
+    """Time the FP64 CPU oracle: `vcycles` V-cycles plus a residual on the sample
+    problem; return (unknowns * V-cycles / s, seconds, description)."""
+    import numpy as np
+
+    import oracle
+    from paper_1307_2036_gb300 import inputs
+    kind, n, nz, graded, w2, l2 = sample
+    og = oracle.Grid(kind, n, nz, inputs.radial_levels(nz, graded=graded), w2, l2)
+    f = rhs_for(kind, n, nz, "smooth_gauss" if kind == 1 else "uniform")
+    b = og.volumes() * f
+    u = np.zeros_like(b)
+    t0 = time.perf_counter()
+    for _ in range(vcycles):
+        u = og.vcycle(b, u)
+    og.residual(b, u)
+    dt = time.perf_counter() - t0
+    N = b.size
+    desc = (f"oracle (plain C, FP64, 1 thread): {vcycles} V-cycle(s) + residual on the "
+            f"{'sphere 6x' if kind == 1 else 'box '}{n}x{n}x{nz} graded grid ({N} unknowns)")
+    return N * vcycles / dt, dt, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    rates, times, desc = [], [], ""
+    for i in range(args.warmup + args.steps):
+        r, dt, desc = oracle_rate(ORACLE_SAMPLE, 1)
+        if i >= args.warmup:
+            rates.append(r)
+            times.append(dt)
+    value = sum(ORACLE_SAMPLE[1] ** 2 * 6 * ORACLE_SAMPLE[2] for _ in times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns*V-cycles/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "unknowns*V-cycles/s", "cores": 1,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "unknowns*V-cycles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1307_2036_gb300 import ellsolve, inputs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    kind, n, nz, graded, w2, l2, rhs_kind, rtol = WORKLOADS[args.workload]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sv = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=graded), w2, l2,
+                             precision=1, use_graph=1, stream=stream.cuda_stream)
+        f_host = torch.from_numpy(rhs_for(kind, n, nz, rhs_kind, member=rank)).pin_memory()
+        f = f_host.to("cuda", non_blocking=True)
+        x = torch.zeros_like(f)
+        x_host = torch.empty_like(f_host).pin_memory()
+    stream.synchronize()
+    N = sv.N
+
+    def solve():
+        st, res = sv.solve(f, x, rtol=rtol, maxit=60)
+        if st < 0:
+            raise RuntimeError(f"solve failed: {st}")
+        return res
+
+    for _ in range(args.warmup):
+        res = solve()
+    vcycles_per_solve = res.iterations
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-timed region: K solves with inputs resident in HBM
+    sampler = ClockSampler(local_rank)
+    barrier()
+    sampler.start()
+    l0 = sv.launch_count()
+    sv.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cycles = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        cycles += solve().iterations
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = sv.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    prof_ms, prof_n, prof_bytes = sv.profile_read()
+    sv.profile(False)
+    final_rel = res.rel_residual
+
+    # end-to-end region: pinned host rhs -> device, solve, solution -> pinned host
+    barrier()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_cycles = 0
+    h0.record(stream)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            f.copy_(f_host, non_blocking=True)
+        e2e_cycles += solve().iterations
+        with torch.cuda.stream(stream):
+            x_host.copy_(x, non_blocking=True)
+    h1.record(stream)
+    barrier()
+    ms_e2e = h0.elapsed_time(h1)
+
+    t = torch.tensor([ms, ms_e2e, float(cycles), float(e2e_cycles)], dtype=torch.float64,
+                     device="cuda")
+    if dist is not None:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, ms_e2e = float(tmax[0]), float(tmax[1])
+        cycles, e2e_cycles = float(tsum[2]), float(tsum[3])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    value = N * cycles / (ms * 1e-3)
+    e2e = N * e2e_cycles / (ms_e2e * 1e-3)
+    peak, peak_kind = measured_peaks()
+    achieved = (prof_bytes / (prof_ms * 1e-3) / 1e9) if prof_ms > 0 else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "smoother_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as fh:
+            tinfo = json.load(fh)
+        if tinfo.get("workload") == args.workload and tinfo.get("kernel_rev") == KERNEL_REV:
+            traffic = tinfo.get("dram_bytes_per_launch")
+    cpu_rate, cpu_s, cpu_desc = oracle_rate(ORACLE_SAMPLE, 1) if not args.no_cpu else (None, 0, "")
+    line = {
+        "metric": METRIC, "value": value, "unit": "unknowns*V-cycles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {
+            "workload": args.workload, "grid": ("cubed sphere 6x" if kind == 1 else "box ") +
+            f"{n}x{n}", "nz": nz, "unknowns": N, "omega2": w2, "lambda": l2 ** 0.5,
+            "solver": "FP32 V-cycle (2/2 line-Jacobi, rho 0.8) in FP64 refinement, CUDA graph",
+            "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
+            "final_rel_residual": final_rel, "time_to_rtol_ms": ms / args.steps,
+            "l2_policy": "inputs larger than L2 (FP32 hierarchy %.1f GB)" % (N * 16 / 3 * 4 / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "k_smooth<float> finest level (line-Jacobi sweep)",
+                     "launches_timed": prof_n, "peak_source": peak_kind},
+        "cpu_baseline": {"value": cpu_rate, "unit": "unknowns*V-cycles/s", "cores": 1,
+                         "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": e2e, "unit": "unknowns*V-cycles/s", "h2d_bytes_per_step": N * 8,
+                "d2h_bytes_per_step": N * 8},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# bumped whenever the finest-level smoother kernel changes (invalidates traffic)
+KERNEL_REV = "smooth-v1"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sphere512")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

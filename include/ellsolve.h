@@ -154,10 +154,15 @@ ellsolve_status ellsolve_level_restrict_residual(ellsolve_t h, int level, int fp
 ellsolve_status ellsolve_level_prolong_add(ellsolve_t h, int level, int fp32, const void *u_c,
                                            void *u);
 
-/* ---- profiling: CUDA-event time of the finest-level smoother launches ---- */
+/* ---- profiling: CUDA-event time of the finest-level smoother launches ----
+ * enable != 0 starts recording an event pair around every finest-level
+ * line-smoother launch on the handle's stream (and resets the totals).
+ * profile_read returns the summed event time, the number of launches timed
+ * and their summed algorithmic bytes: per unknown, a sweep reads u and b and
+ * writes u (3 words), or reads b and writes u when the iterate is zero (2). */
 ellsolve_status ellsolve_profile_enable(ellsolve_t h, int enable);
 ellsolve_status ellsolve_profile_read(ellsolve_t h, double *smoother_ms_total, int *launches,
-                                      double *bytes_per_launch);
+                                      double *bytes_total);
 /* number of kernel launches the library issued on this handle so far */
 uint64_t ellsolve_launch_count(ellsolve_t h);
 

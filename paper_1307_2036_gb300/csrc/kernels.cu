@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
 // ---------------------------------------------------------------------------
 // FP64 outer residual of the iterative refinement.
 // ---------------------------------------------------------------------------
+template <bool XZERO>
 __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restrict__ L64,
                                                       const Lv<float> *__restrict__ L32,
                                                       const Item *__restrict__ items,
@@ -299,14 +300,16 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         float *__restrict__ r32 = L32[it.lv].b;
         const double sc = scale[it.lv];
         const Column<double> col = load_column(d, c);
-        double um = 0.0, u0 = __ldg(x + c), up = 0.0, gk = __ldg(g);
+        double um = 0.0, u0 = XZERO ? 0.0 : __ldg(x + c), up = 0.0, gk = __ldg(g);
 #pragma unroll 2
         for (int k = 0; k < nz; ++k) {
             const size_t o = size_t(k) * nc;
             const double Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
-            up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
-            const double r = col.A * (Vk * __ldg(f + o + c)) -
-                             stencil(col, x + o, u0, um, up, Vk, gk, gk1);
+            double r = col.A * (Vk * __ldg(f + o + c));
+            if (!XZERO) {
+                up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
+                r -= stencil(col, x + o, u0, um, up, Vk, gk, gk1);
+            }
             r32[o + c] = float(r * sc);
             acc += r * r;
             um = u0;
@@ -561,9 +564,10 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
-                               double *partials) {
+                               double *partials, int x_is_zero) {
     if (nitems <= 0) return cudaSuccess;
-    k_ir_residual<<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
+    if (x_is_zero) k_ir_residual<true><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
+    else k_ir_residual<false><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
     return cudaGetLastError();
 }
 

@@ -34,9 +34,10 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 // Iterative-refinement outer step, per member m (items' lv = member index):
 //   r = A_P V_k f - A x   in FP64, f = L64[m].b (pointwise), x = L64[m].u[0],
 //   L32[m].b = float(r * scale[m]), partials[item] = sum of r^2.
+// x_is_zero: x = 0, so r = A_P V_k f without the stencil (start of a solve).
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
-                               double *partials);
+                               double *partials, int x_is_zero);
 // x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with active[m] != 0
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,

@@ -68,6 +68,7 @@ Problem::~Problem() {
     plan.reset();
     batch_plan.reset();
     if (pinned) cudaFreeHost(pinned);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto &e : ev_free) cudaEventDestroy(e);
     for (auto &e : ev_graph) cudaEventDestroy(e);
 }
@@ -318,7 +319,11 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
             s.cur[l] ^= 1;
             s.zero[l] = 0;
             op.max_nz = std::max(op.max_nz, mem[m]->nz);
-            if (l == 0) op.finest = true;
+            if (l == 0) {
+                op.finest = true;
+                const double w = precision == 1 ? 4.0 : 8.0;
+                op.bytes += (items.back().zero ? 2.0 : 3.0) * w * double(mem[m]->N);
+            }
         }
         op.n = int(items.size()) - op.off;
         prog.ops.push_back(op);
@@ -427,7 +432,7 @@ static void run_program(Plan &pl, const Program &prog) {
                 const bool timed = p0.prof && op.finest;
                 if (timed) p0.prof_mark_begin(s);
                 check_cuda(launch_smooth<T>(s, L, it + op.off, op.n, T(op.rho), op.max_nz), "smooth");
-                if (timed) p0.prof_mark_end(s);
+                if (timed) p0.prof_mark_end(s, op.bytes);
                 count(pl);
                 break;
             }
@@ -469,28 +474,32 @@ void Problem::prof_mark_begin(cudaStream_t s) {
                "event record");
 }
 
-void Problem::prof_mark_end(cudaStream_t s) {
+void Problem::prof_mark_end(cudaStream_t s, double bytes) {
     std::vector<cudaEvent_t> &pool = capturing ? ev_graph : ev_free;
+    std::vector<double> &pb = capturing ? ev_graph_bytes : ev_free_bytes;
     int &next = capturing ? ev_graph_used : ev_next;
     check_cuda(cudaEventRecordWithFlags(pool[next + 1], s, capturing ? cudaEventRecordExternal : 0),
                "event record");
+    if (int(pb.size()) < next / 2 + 1) pb.resize(next / 2 + 1);
+    pb[next / 2] = bytes;
     next += 2;
 }
 
 void Problem::prof_collect(bool graph_replayed) {
     if (!prof) return;
     check_cuda(cudaStreamSynchronize(stream), "prof sync");
-    auto read = [&](std::vector<cudaEvent_t> &pool, int used) {
+    auto read = [&](std::vector<cudaEvent_t> &pool, const std::vector<double> &pb, int used) {
         for (int i = 0; i + 1 < used; i += 2) {
             float ms = 0.f;
             check_cuda(cudaEventElapsedTime(&ms, pool[i], pool[i + 1]), "elapsed");
             prof_ms += ms;
+            prof_bytes += pb[i / 2];
             prof_count += 1;
         }
     };
-    read(ev_free, ev_next);
+    read(ev_free, ev_free_bytes, ev_next);
     ev_next = 0;
-    if (graph_replayed) read(ev_graph, ev_graph_used);
+    if (graph_replayed) read(ev_graph, ev_graph_bytes, ev_graph_used);
 }
 
 // ---------------------------------------------------------------------------
@@ -624,13 +633,13 @@ static void ir_outer_descs(Plan &pl, const std::vector<const double *> &f,
     }
 }
 
-static void ir_residual_norm(Plan &pl, int op) {
+static void ir_residual_norm(Plan &pl, int op, int x_is_zero = 0) {
     cudaStream_t s = pl.mem[0]->stream;
     const Item *it = pl.ditems.as<Item>();
     const int M = int(pl.mem.size());
     check_cuda(launch_ir_residual(s, pl.outer64.as<Lv<double>>(), pl.fine32.as<Lv<float>>(),
                                   it + pl.outer_off, pl.outer_n, pl.scales.as<double>(),
-                                  pl.partials.as<double>()),
+                                  pl.partials.as<double>(), x_is_zero),
                "ir_residual");
     check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>(), M,
                                pl.norms.as<double>(), op, op == 2 ? pl.scales.as<double>() : nullptr,
@@ -674,22 +683,39 @@ static void ir_step_graph(Plan &pl) {
         pl.sync_items();
     }
     if (!pl.gexec) {
-        for (Problem *p : pl.mem) p->capturing = true;
+        // Capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph is launched on the
+        // caller's stream below.
+        if (!p0.cap_stream)
+            check_cuda(cudaStreamCreateWithFlags(&p0.cap_stream, cudaStreamNonBlocking),
+                       "capture stream");
+        cudaStream_t cs = p0.cap_stream;
+        for (Problem *p : pl.mem) {
+            p->capturing = true;
+            p->stream = cs;
+        }
+        auto restore = [&]() {
+            for (Problem *p : pl.mem) {
+                p->capturing = false;
+                p->stream = s;
+            }
+        };
         const uint64_t before = p0.launches;
         p0.ev_graph_used = 0;
-        check_cuda(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+        check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
         try {
             ir_step(pl);
         } catch (...) {
             cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(s, &g);
+            cudaStreamEndCapture(cs, &g);
             if (g) cudaGraphDestroy(g);
-            for (Problem *p : pl.mem) p->capturing = false;
+            restore();
             throw;
         }
         cudaGraph_t graph = nullptr;
-        check_cuda(cudaStreamEndCapture(s, &graph), "end capture");
-        for (Problem *p : pl.mem) p->capturing = false;
+        cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        restore();
+        check_cuda(ec, "end capture");
         cudaError_t e = cudaGraphInstantiate(&pl.gexec, graph, 0);
         cudaGraphDestroy(graph);
         check_cuda(e, "graph instantiate");
@@ -721,11 +747,11 @@ ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
                                cudaMemcpyHostToDevice, s),
                "active reset");
     // ||b|| (x = 0 so the residual is b) and the FP32 scaling sqrt(N)/||b||
-    ir_residual_norm(pl, 2);
+    ir_residual_norm(pl, 2, 1);
     read_norms(pl, M);
     std::vector<double> bnorm = pl.host_norms;
     // residual with the final scaling (x = 0 still)
-    ir_residual_norm(pl, 1);
+    ir_residual_norm(pl, 1, 1);
     std::vector<std::vector<double>> hist(M, std::vector<double>{1.0});
     std::vector<int> iters(M, 0);
     std::vector<char> active(M, 1);
@@ -1172,6 +1198,7 @@ ellsolve_status ellsolve_profile_enable(ellsolve_t h, int enable) {
     if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
     h->prof = enable != 0;
     h->prof_ms = 0.0;
+    h->prof_bytes = 0.0;
     h->prof_count = 0;
     h->ev_next = 0;
     if (h->plan) h->plan->drop_graph();
@@ -1184,9 +1211,7 @@ ellsolve_status ellsolve_profile_read(ellsolve_t h, double *ms, int *launches, d
     if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
     if (ms) *ms = h->prof_ms;
     if (launches) *launches = int(h->prof_count);
-    // algorithmic bytes of one finest-level sweep: read u and b, write u (3 words per unknown)
-    const size_t w = h->opts.precision == 1 ? 4 : 8;
-    if (bytes) *bytes = double(3 * w * h->N);
+    if (bytes) *bytes = h->prof_bytes;
     return ELLSOLVE_OK;
     ELLS_GUARD_END
 }

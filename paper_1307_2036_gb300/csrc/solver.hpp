@@ -66,6 +66,7 @@ struct Op {
     double rho = 1.0;         // smoother damping
     int max_nz = 0;           // largest nz among the items
     bool finest = false;      // smooths a finest level (profiled)
+    double bytes = 0.0;       // algorithmic bytes of the finest-level work
     int member = 0, level = 0, buf = 0;  // kMemset target
 };
 
@@ -116,7 +117,8 @@ struct Problem {
     std::vector<double> r;
     int nz = 0, P = 1, nlev = 0;
     size_t N = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // the caller's stream: all work is ordered on it
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     std::vector<LevelStore> lev;
     DevBuf V64, g64, V32, g32;
     std::vector<Lv<double>> h64;
@@ -131,8 +133,9 @@ struct Problem {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_graph;
     int ev_next = 0, ev_graph_used = 0;
-    double prof_ms = 0.0;
+    double prof_ms = 0.0, prof_bytes = 0.0;
     long prof_count = 0;
+    std::vector<double> ev_free_bytes, ev_graph_bytes;  // bytes per recorded pair
 
     ~Problem();
     void build(const ellsolve_grid &g, double w2, double l2, const double *r_levels,
@@ -140,7 +143,7 @@ struct Problem {
     Plan &single_plan();
     size_t footprint_bytes() const;
     void prof_mark_begin(cudaStream_t s);
-    void prof_mark_end(cudaStream_t s);
+    void prof_mark_end(cudaStream_t s, double bytes);
     void prof_collect(bool graph_replayed);
 };
 

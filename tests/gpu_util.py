@@ -21,6 +21,26 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def sensitivity(fn, *arrays, trials=2, seed=0, ulps=4):
+    """Relative L2 change of fn's output when each input is perturbed by random
+    relative amounts of up to `ulps` machine epsilons: how far two correct FP64
+    evaluations of the same map can drift apart from rounding alone."""
+    eps = np.finfo(np.float64).eps
+    base = fn(*arrays)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(trials):
+        pert = [a * (1.0 + ulps * eps * rng.uniform(-1.0, 1.0, np.shape(a))) for a in arrays]
+        worst = max(worst, rel_l2(fn(*pert), base))
+    return worst
+
+
+def fp64_tol(fn, *arrays, floor=1e-13):
+    """Tolerance of an FP64 parity check: 16x the oracle's own rounding
+    sensitivity, at least `floor`."""
+    return max(floor, 16.0 * sensitivity(fn, *arrays))
+
+
 class Pair:
     """An oracle grid and a library solver for the same problem."""
 
