@@ -32,6 +32,7 @@ METRIC = "unknowns*V-cycles/s"
 WORKLOADS = {
     # name: (kind, n, nz, graded, omega2, lambda2, rhs, rtol)
     "sphere512": (1, 512, 128, True, 0.01, 1.0, "smooth_gauss", 1e-5),
+    "sphere256": (1, 256, 128, True, 0.01, 1.0, "smooth_gauss", 1e-5),
     "sphere128": (1, 128, 128, True, 0.01, 1.0, "smooth_gauss", 1e-5),
     "box256": (0, 256, 64, True, 0.01, 1.0, "uniform", 1e-5),
 }
@@ -283,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
-KERNEL_REV = "smooth-v1"
+KERNEL_REV = "smooth-v6-rcpapprox"
 
 
 def main():

@@ -9,7 +9,7 @@ namespace ells {
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<double> { using type = double4_32a; };
 
 // One multigrid level of one problem ("member"), in precision T.  Vectors are
 // [nz][ncol] with the column index fastest.  The radial vectors belong to the

@@ -14,10 +14,20 @@
 // against the large vertical coupling.
 #include "kernels.hpp"
 
+#include <map>
+#include <mutex>
+
 namespace ells {
 namespace {
 
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// Reciprocal of a Thomas pivot.  FP32 (the inner smoother of the iterative
+// refinement): the hardware approximation, within one ulp, in one instruction
+// on the critical path of the recurrence.  FP64: correctly rounded.
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -78,6 +88,28 @@ __device__ __forceinline__ T stencil(const Column<T> &col, const T *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global->shared copies (cp.async, per thread).  A copy with
+// `ok` false writes zeros and reads nothing (source size 0).  Completion is
+// tracked per thread with commit/wait groups, so no spin-wait is involved.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void cp_async(T *smem, const T *gmem, bool ok) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    const int n = ok ? int(sizeof(T)) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Line smoother (Sec. 3.2, Eq. BlockRBSOR with the Jacobi ordering; Algorithm
 // Thomas per column): u_out = u_in + rho Dtilde^{-1} (b - A u_in).
 // Forward sweep k = 0..nz-1: residual on the fly and the elimination; the
@@ -86,10 +118,24 @@ __device__ __forceinline__ T stencil(const Column<T> &col, const T *__restrict__
 // (CPS) or in the level's aux buffer.  The pivot is formed as the diagonal-
 // dominance excess eps_k = V_k s + lo_k eps_{k-1}/m_{k-1} plus up_k (the same
 // Thomas recurrence without cancellation, needed in FP32).
+//
+// Each thread walks its column sequentially.  The values of level k (own u_k+1
+// and b_k, the four neighbours' u_k) are fetched kRing-1 levels ahead by
+// per-thread cp.async copies into a shared-memory ring, so the sweep streams
+// at HBM rate with two CTAs per SM; the back substitution prefetches f'_k and
+// u_k the same way.  ZERO: u_in = 0 (not read); 2: decided per item.
 // ---------------------------------------------------------------------------
-template <typename T, bool CPS>
+constexpr int kRing = 16;  // ring depth (levels in flight + 1)
+
+template <typename T>
+__host__ __device__ constexpr size_t smooth_ring_bytes() {
+    return size_t(kRing) * 6 * kBlk * sizeof(T);
+}
+
+template <typename T, bool CPS, int ZERO>
 __global__ void __launch_bounds__(kBlk) k_smooth(const Lv<T> *__restrict__ L,
-                                                 const Item *__restrict__ items, T rho) {
+                                                 const Item *__restrict__ items, T rho,
+                                                 int cp_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Item it = items[blockIdx.x];
     const Lv<T> &d = L[it.lv];
@@ -97,7 +143,7 @@ __global__ void __launch_bounds__(kBlk) k_smooth(const Lv<T> *__restrict__ L,
     const int nc = d.ncol;
     if (c >= nc) return;
     const int nz = d.nz;
-    const int zero = it.zero;
+    const bool zero = ZERO == 2 ? (it.zero != 0) : (ZERO == 1);
     const T *__restrict__ u = d.u[it.in];
     T *__restrict__ un = d.u[it.out];
     const T *__restrict__ b = d.b;
@@ -112,21 +158,56 @@ __global__ void __launch_bounds__(kBlk) k_smooth(const Lv<T> *__restrict__ L,
         cp = d.aux + c;
         cps = nc;
     }
+    // ring[slot][field][thread]; fields 0 u_{k+1}, 1 b_k, 2..5 neighbours of level k
+    T *ring = reinterpret_cast<T *>(smem_raw + cp_bytes) + threadIdx.x;
     const Column<T> col = load_column(d, c);
+    const size_t snc = size_t(nc);
+
+    auto issue = [&](int k) {
+        T *sl = ring + (k % kRing) * 6 * kBlk;
+        const bool ok = k < nz;
+        const size_t o = ok ? size_t(k) * snc : 0;
+        cp_async(sl + kBlk, b + o + c, ok);
+        if (!zero) {
+            const bool ok1 = k + 1 < nz;
+            cp_async(sl, u + (ok1 ? o + snc : 0) + c, ok1);
+            const T *row = u + o;
+            cp_async(sl + 2 * kBlk, row + col.nb.x, ok);
+            cp_async(sl + 3 * kBlk, row + col.nb.y, ok);
+            cp_async(sl + 4 * kBlk, row + col.nb.z, ok);
+            cp_async(sl + 5 * kBlk, row + col.nb.w, ok);
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll 1
+    for (int k = 0; k < kRing - 1; ++k) issue(k);
 
     T ratio = T(0), fp = T(0);
-    T um = T(0), u0 = T(0), up = T(0);
-    if (!zero) u0 = __ldg(u + c);
+    T um = T(0), u0 = zero ? T(0) : __ldg(u + c);
     T gk = __ldg(g);
-#pragma unroll 4
+#pragma unroll 2
     for (int k = 0; k < nz; ++k) {
-        const size_t o = size_t(k) * nc;
+        cp_async_wait<kRing - 2>();  // level k has landed
+        const T *sl = ring + (k % kRing) * 6 * kBlk;
+        const T rb = sl[kBlk];
+        T up = T(0), nw = T(0), ne = T(0), ns = T(0), nn = T(0);
+        if (!zero) {
+            up = sl[0];
+            nw = sl[2 * kBlk];
+            ne = sl[3 * kBlk];
+            ns = sl[4 * kBlk];
+            nn = sl[5 * kBlk];
+        }
+        issue(k + kRing - 1);
         const T Vk = __ldg(V + k);
         const T gk1 = __ldg(g + k + 1);
-        T r = __ldg(b + o + c);
+        T r = rb;
         if (!zero) {
-            up = (k + 1 < nz) ? __ldg(u + o + nc + c) : T(0);
-            r -= stencil(col, u + o, u0, um, up, Vk, gk, gk1);
+            const T horiz = (col.t0 * (u0 - nw) + col.t1 * (u0 - ne)) +
+                            (col.t2 * (u0 - ns) + col.t3 * (u0 - nn));
+            const T vert = gk1 * (u0 - up) + gk * (u0 - um);
+            r -= col.A * (Vk * u0) + Vk * horiz + col.A * vert;
             um = u0;
             u0 = up;
         }
@@ -135,18 +216,281 @@ __global__ void __launch_bounds__(kBlk) k_smooth(const Lv<T> *__restrict__ L,
         const T inv = rcp(eps + hi);
         fp = (r + lo * fp) * inv;
         cp[size_t(k) * cps] = hi * inv;
-        un[o + c] = fp;
+        un[size_t(k) * snc + c] = fp;
         ratio = eps * inv;
         gk = gk1;
     }
+    cp_async_wait<0>();
+    __threadfence_block();  // f'_k stores are seen by the copies below
+
+    // back substitution k = nz-1 .. 0; ring fields 0 f'_k, 1 u_k
+    auto issue_back = [&](int j) {
+        const int k = nz - 1 - j;
+        T *sl = ring + (j % kRing) * 6 * kBlk;
+        const bool ok = k >= 0;
+        const size_t o = ok ? size_t(k) * snc : 0;
+        cp_async(sl, un + o + c, ok);
+        if (!zero) cp_async(sl + kBlk, u + o + c, ok);
+        cp_async_commit();
+    };
+#pragma unroll 1
+    for (int j = 0; j < kRing - 1; ++j) issue_back(j);
     T x = T(0);
-#pragma unroll 4
-    for (int k = nz - 1; k >= 0; --k) {
-        const size_t o = size_t(k) * nc;
-        x = un[o + c] + cp[size_t(k) * cps] * x;
-        const T uo = zero ? T(0) : __ldg(u + o + c);
-        un[o + c] = uo + rho * x;
+#pragma unroll 2
+    for (int j = 0; j < nz; ++j) {
+        const int k = nz - 1 - j;
+        cp_async_wait<kRing - 2>();
+        const T *sl = ring + (j % kRing) * 6 * kBlk;
+        const T fk = sl[0];
+        const T uo = zero ? T(0) : sl[kBlk];
+        issue_back(j + kRing - 1);
+        x = fk + cp[size_t(k) * cps] * x;
+        __stcs(un + size_t(k) * snc + c, uo + rho * x);
     }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// Line smoother, row-staged variant for FP32 levels with n % 4 == 0,
+// ncol % 4 == 0 and nz % 8 == 0 (every fine level of the configurations).
+//
+// Same sweep and arithmetic as k_smooth, with the data movement organised per
+// warp: for level k a warp (32 consecutive columns) needs its own row of u
+// with one column of halo on each side, its row of b, and the rows j-1 and j+1
+// (columns c -/+ n).  These are 34 aligned 16-byte chunks, copied with one
+// cp.async per lane (two for lanes 0 and 1) into a ring of kFR levels in
+// shared memory; each lane keeps running pointers, so a level costs a handful
+// of instructions.  Columns whose neighbour across a face is not the adjacent
+// column of the staged rows (panel edges, periodic wrap) fetch it through the
+// neighbour table into a per-thread slot; only warps containing such a column
+// take that branch.  c'_k lives in shared memory as in k_smooth.
+// ---------------------------------------------------------------------------
+constexpr int kFR = 8;      // ring depth (levels)
+constexpr int kRowF = 136;  // floats per warp and slot: [own 40][b 32][j-1 32][j+1 32]
+constexpr int kOwnO = 0, kBO = 40, kJmO = 72, kJpO = 104;
+
+__host__ __device__ inline size_t rows_smem_bytes(int max_nz) {
+    return size_t(kBlk) * max_nz * 4 + size_t(kFR) * 4 * kRowF * 4 + size_t(kFR) * 2 * kBlk * 4 +
+           size_t(2 * max_nz + 1) * 4;
+}
+
+__device__ __forceinline__ void cp_async16(float *smem, const float *gmem, int nbytes) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes)
+                 : "memory");
+}
+
+// wait until at most n (a constant after unrolling) copy groups are pending
+__device__ __forceinline__ void cp_async_wait_upto(int n) {
+    switch (n < 0 ? 0 : n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        case 5: cp_async_wait<5>(); break;
+        default: cp_async_wait<6>(); break;
+    }
+}
+
+template <int ZERO>
+__global__ void __launch_bounds__(kBlk) k_smooth_rows(const Lv<float> *__restrict__ L,
+                                                      const Item *__restrict__ items, float rho,
+                                                      int max_nz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *cps = reinterpret_cast<float *>(smem_raw);  // c'[k][thread]
+    float *ring = cps + kBlk * max_nz;
+    float *fbr = ring + kFR * 4 * kRowF;
+    float *rad = fbr + kFR * 2 * kBlk;
+    const Item it = items[blockIdx.x];
+    const Lv<float> &d = L[it.lv];
+    const int nc = d.ncol, nz = d.nz, n = d.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = it.col0 + tid;
+    const int c0w = it.col0 + 32 * warp;
+    const bool active = c < nc;
+    constexpr bool zero = ZERO == 1;
+    for (int i = tid; i < nz; i += kBlk) rad[i] = d.V[i];
+    for (int i = tid; i <= nz; i += kBlk) rad[nz + i] = d.g[i];
+    __syncthreads();
+    const float *Vs = rad, *gs = rad + nz;
+    const float *__restrict__ u = d.u[it.in];
+    float *__restrict__ un = d.u[it.out];
+    const float *__restrict__ b = d.b;
+    const size_t snc = size_t(nc);
+
+    // this lane's chunk copies: primary chunk q = lane, secondary q = 32 + lane (lanes 0, 1)
+    auto chunk = [&](int q, const float *&src, int &dst, int &nbytes) {
+        int scol;
+        bool use;
+        if (q < 10) {
+            src = u; scol = c0w - 4 + 4 * q; dst = kOwnO + 4 * q; use = !zero;
+        } else if (q < 18) {
+            src = b; scol = c0w + 4 * (q - 10); dst = kBO + 4 * (q - 10); use = true;
+        } else if (q < 26) {
+            src = u; scol = c0w - n + 4 * (q - 18); dst = kJmO + 4 * (q - 18); use = !zero;
+        } else {
+            src = u; scol = c0w + n + 4 * (q - 26); dst = kJpO + 4 * (q - 26); use = !zero;
+        }
+        use = use && scol >= 0 && scol + 4 <= nc;
+        src = use ? src + scol : b;  // an unused copy reads nothing (size 0)
+        nbytes = use ? 16 : 0;
+    };
+    const float *p1, *p2;
+    int dst1, dst2, nb1, nb2;
+    chunk(lane, p1, dst1, nb1);
+    chunk(32 + (lane & 1), p2, dst2, nb2);
+    const bool two = lane < 2;
+    if (!two) nb2 = 0;
+    const int adv1 = nb1 ? nc : 0, adv2 = nb2 ? nc : 0;
+
+    // stencil constants and the (at most two) neighbours outside the staged rows
+    Column<float> col;
+    col.A = 1.f; col.t0 = col.t1 = col.t2 = col.t3 = 0.f; col.s = 1.f;
+    col.nb = make_int4(0, 0, 0, 0);
+    int fd0 = -1, fd1 = -1;
+    const float *pf0 = u, *pf1 = u;
+    if (active) {
+        col = load_column(d, c);
+        const int want[4] = {c - 1, c + 1, c - n, c + n};
+        const int have[4] = {col.nb.x, col.nb.y, col.nb.z, col.nb.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (have[q] != want[q]) {
+                if (fd0 < 0) {
+                    fd0 = q;
+                    pf0 = u + have[q];
+                } else if (fd1 < 0) {
+                    fd1 = q;
+                    pf1 = u + have[q];
+                }
+            }
+    }
+    const bool warp_fb = !zero && __any_sync(0xffffffffu, fd0 >= 0);
+    const int nbf0 = fd0 >= 0 ? 4 : 0, nbf1 = fd1 >= 0 ? 4 : 0;
+    float *wring = ring + warp * kRowF;
+    float *s1 = wring + dst1, *s2 = wring + dst2;
+    float *f0s = fbr + tid, *f1s = fbr + kBlk + tid;
+
+    // copy level (next issue) into ring slot `slot` and advance the pointers
+    auto issue = [&](int slot) {
+        cp_async16(s1 + slot * 4 * kRowF, p1, nb1);
+        p1 += adv1;
+        if (two) {
+            cp_async16(s2 + slot * 4 * kRowF, p2, nb2);
+            p2 += adv2;
+        }
+        if (warp_fb) {
+            cp_async(f0s + slot * 2 * kBlk, pf0, nbf0 != 0);
+            cp_async(f1s + slot * 2 * kBlk, pf1, nbf1 != 0);
+            pf0 += snc;
+            pf1 += snc;
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll
+    for (int j = 0; j < kFR - 1; ++j) issue(j);
+    float u0 = 0.f, um = 0.f;
+    if (!zero) {
+        cp_async_wait<kFR - 2>();
+        __syncwarp();
+        u0 = wring[kOwnO + 4 + lane];
+    }
+    float ratio = 0.f, fp = 0.f, gk = gs[0];
+    float *fpo = un + c;
+    float *cpw = cps + tid;
+    const int nblk = nz / kFR;
+#pragma unroll 1
+    for (int kb = 0; kb < nblk; ++kb) {
+        const bool last = kb == nblk - 1;
+#pragma unroll
+        for (int j = 0; j < kFR; ++j) {
+            const int k = kb * kFR + j;
+            __syncwarp();
+            if (!last) {
+                issue((j + kFR - 1) & (kFR - 1));
+                cp_async_wait<kFR - 2>();
+            } else {
+                if (j == 0) issue(kFR - 1);
+                cp_async_wait_upto(kFR - 2 - j);
+            }
+            __syncwarp();
+            const float *sk = wring + j * 4 * kRowF;
+            float r = sk[kBO + lane];
+            const float gk1 = gs[k + 1], Vk = Vs[k];
+            if (!zero) {
+                const float up = (last && j == kFR - 1) ? 0.f
+                                                        : wring[((j + 1) & (kFR - 1)) * 4 * kRowF +
+                                                                kOwnO + 4 + lane];
+                float nw = sk[kOwnO + 3 + lane], ne = sk[kOwnO + 5 + lane];
+                float ns = sk[kJmO + lane], nn = sk[kJpO + lane];
+                if (warp_fb) {
+                    const float v0 = f0s[j * 2 * kBlk], v1 = f1s[j * 2 * kBlk];
+                    nw = fd0 == 0 ? v0 : (fd1 == 0 ? v1 : nw);
+                    ne = fd0 == 1 ? v0 : (fd1 == 1 ? v1 : ne);
+                    ns = fd0 == 2 ? v0 : (fd1 == 2 ? v1 : ns);
+                    nn = fd0 == 3 ? v0 : (fd1 == 3 ? v1 : nn);
+                }
+                const float horiz = (col.t0 * (u0 - nw) + col.t1 * (u0 - ne)) +
+                                    (col.t2 * (u0 - ns) + col.t3 * (u0 - nn));
+                const float vert = gk1 * (u0 - up) + gk * (u0 - um);
+                r -= col.A * (Vk * u0) + Vk * horiz + col.A * vert;
+                um = u0;
+                u0 = up;
+            }
+            const float lo = col.A * gk, hi = col.A * gk1;
+            const float eps = Vk * col.s + lo * ratio;
+            const float inv = rcp(eps + hi);
+            fp = (r + lo * fp) * inv;
+            cpw[k * kBlk] = hi * inv;
+            if (active) fpo[size_t(k) * snc] = fp;
+            ratio = eps * inv;
+            gk = gk1;
+        }
+    }
+    __threadfence_block();  // the f'_k stores of this warp are seen by its copies below
+    __syncwarp();
+
+    // back substitution: slot fields [own 0..31] = f'_k, [b 0..31] = u_k
+    const bool bf = lane < 8, bu = !zero && lane >= 8 && lane < 16;
+    const int bcol = c0w + 4 * (lane & 7);
+    const int nbb = ((bf || bu) && bcol + 4 <= nc) ? 16 : 0;
+    const float *pb = nbb ? (bf ? un : u) + size_t(nz - 1) * snc + bcol : b;
+    const int advb = nbb ? nc : 0;
+    float *sb = wring + (bf ? kOwnO : kBO) + 4 * (lane & 7);
+    auto issue_back = [&](int slot) {
+        cp_async16(sb + slot * 4 * kRowF, pb, nbb);
+        pb -= advb;
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < kFR - 1; ++j) issue_back(j);
+    float x = 0.f;
+#pragma unroll 1
+    for (int kb = 0; kb < nblk; ++kb) {
+        const bool last = kb == nblk - 1;
+#pragma unroll
+        for (int j = 0; j < kFR; ++j) {
+            const int jj = kb * kFR + j;  // levels from the top
+            const int k = nz - 1 - jj;
+            __syncwarp();
+            if (!last) {
+                issue_back((j + kFR - 1) & (kFR - 1));
+                cp_async_wait<kFR - 1>();  // level jj has landed
+            } else {
+                if (j == 0) issue_back(kFR - 1);
+                cp_async_wait_upto(kFR - 1 - j);
+            }
+            __syncwarp();
+            const float *sk = wring + j * 4 * kRowF;
+            const float fk = sk[kOwnO + lane];
+            const float uo = zero ? 0.f : sk[kBO + lane];
+            x = fk + cpw[k * kBlk] * x;
+            if (active) __stcs(un + size_t(k) * snc + c, uo + rho * x);
+        }
+    }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -505,14 +849,21 @@ __global__ void k_cg_scalars(double *scalars, const double *sums, int op) {
     }
 }
 
+// Opt a kernel in to more than 48 KB of dynamic shared memory (once per
+// kernel and size; the attribute is per function, so the cache is keyed on
+// the kernel's address).
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-    static size_t configured = 0;
-    if (bytes > 48 * 1024 && bytes > configured) {
+    static std::mutex mu;
+    static std::map<const void *, size_t> configured;
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = configured[reinterpret_cast<const void *>(kernel)];
+    if (bytes > have) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(bytes));
         if (e != cudaSuccess) return e;
-        configured = bytes;
+        have = bytes;
     }
     return cudaSuccess;
 }
@@ -520,21 +871,54 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 // Shared-memory budget for the Thomas coefficients of one block.
-constexpr size_t kSmemCap = 200 * 1024;
+constexpr size_t kSmemCap = 227 * 1024;
+
+template <typename T, int Z>
+static cudaError_t launch_smooth_z(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
+                                   T rho, int max_nz) {
+    const size_t ring = smooth_ring_bytes<T>();
+    const size_t cpb = (size_t(kBlk) * max_nz * sizeof(T) + 15) / 16 * 16;
+    if (sizeof(T) == 4 && cpb + ring <= kSmemCap) {
+        cudaError_t e = set_smem(k_smooth<T, true, Z>, cpb + ring);
+        if (e != cudaSuccess) return e;
+        k_smooth<T, true, Z><<<nitems, kBlk, cpb + ring, s>>>(L, items, rho, int(cpb));
+    } else {
+        cudaError_t e = set_smem(k_smooth<T, false, Z>, ring);
+        if (e != cudaSuccess) return e;
+        k_smooth<T, false, Z><<<nitems, kBlk, ring, s>>>(L, items, rho, 0);
+    }
+    return cudaGetLastError();
+}
+
+template <int Z>
+static cudaError_t launch_rows_z(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                                 float rho, int max_nz, int ctas_per_sm) {
+    size_t bytes = rows_smem_bytes(max_nz);
+    // pad the request to cap the CTAs per SM (bounds the L2 working set)
+    if (ctas_per_sm > 0) {
+        const size_t cap = (size_t(228) * 1024) / size_t(ctas_per_sm) - 1024;
+        if (cap > bytes) bytes = cap;
+    }
+    cudaError_t e = set_smem(k_smooth_rows<Z>, bytes);
+    if (e != cudaSuccess) return e;
+    k_smooth_rows<Z><<<nitems, kBlk, bytes, s>>>(L, items, rho, max_nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                               float rho, int max_nz, int zero_mode, int ctas_per_sm) {
+    if (nitems <= 0) return cudaSuccess;
+    if (zero_mode == 1) return launch_rows_z<1>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
+    return launch_rows_z<0>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
+}
 
 template <typename T>
 cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems, T rho,
-                          int max_nz) {
+                          int max_nz, int zero_mode) {
     if (nitems <= 0) return cudaSuccess;
-    const size_t bytes = size_t(kBlk) * max_nz * sizeof(T);
-    if (sizeof(T) == 4 && bytes <= kSmemCap) {
-        cudaError_t e = set_smem(k_smooth<T, true>, bytes);
-        if (e != cudaSuccess) return e;
-        k_smooth<T, true><<<nitems, kBlk, bytes, s>>>(L, items, rho);
-    } else {
-        k_smooth<T, false><<<nitems, kBlk, 0, s>>>(L, items, rho);
-    }
-    return cudaGetLastError();
+    if (zero_mode == 0) return launch_smooth_z<T, 0>(s, L, items, nitems, rho, max_nz);
+    if (zero_mode == 1) return launch_smooth_z<T, 1>(s, L, items, nitems, rho, max_nz);
+    return launch_smooth_z<T, 2>(s, L, items, nitems, rho, max_nz);
 }
 
 template <typename T>
@@ -628,7 +1012,7 @@ cudaError_t launch_cg_scalars(cudaStream_t s, double *scalars, const double *sum
 
 #define ELLS_INST(T)                                                                            \
     template cudaError_t launch_smooth<T>(cudaStream_t, const Lv<T> *, const Item *, int, T,     \
-                                          int);                                                  \
+                                          int, int);                                             \
     template cudaError_t launch_resid<T>(cudaStream_t, const Lv<T> *, const Item *, int, int,    \
                                          double *);                                              \
     template cudaError_t launch_restrict_resid<T>(cudaStream_t, const Lv<T> *, const Item *,     \

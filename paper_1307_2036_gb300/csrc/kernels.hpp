@@ -9,10 +9,17 @@ namespace ells {
 
 // Line smoother: one damped block-Jacobi sweep on every item of `items`
 // (nitems blocks of kBlk columns).  max_nz: largest nz among the items'
-// descriptors (sizes the shared-memory Thomas scratch).
+// descriptors (sizes the shared-memory Thomas scratch).  zero_mode: 0 no item
+// starts from a zero iterate, 1 all do, 2 mixed (read from each item).
 template <typename T>
 cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems, T rho,
-                          int max_nz);
+                          int max_nz, int zero_mode);
+
+// Row-staged FP32 smoother: valid when every item's level has n % 4 == 0,
+// ncol % 4 == 0 and nz % 8 == 0 and zero_mode is 0 or 1.  ctas_per_sm > 0
+// caps the resident CTAs per SM (through the shared-memory request).
+cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                               float rho, int max_nz, int zero_mode, int ctas_per_sm);
 
 // mode 0: aux = A u[in]; mode 1: aux = b - A u[in]; mode 2: only the partial
 // sums of (b - A u[in])^2 into partials[item] (FP64).

@@ -119,9 +119,9 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
         if (!hl.pst.empty()) upload(L.pst, ps, s);
         const bool lev64 = need64 && (l == 0 || o.precision == 0);
         if (lev64) {
-            std::vector<double4> tr(nc);
+            std::vector<double4_32a> tr(nc);
             for (size_t c = 0; c < nc; ++c)
-                tr[c] = make_double4(hl.trans[4 * c], hl.trans[4 * c + 1], hl.trans[4 * c + 2],
+                tr[c] = make_double4_32a(hl.trans[4 * c], hl.trans[4 * c + 1], hl.trans[4 * c + 2],
                                      hl.trans[4 * c + 3]);
             upload(L.area64, hl.area, s);
             upload(L.tr64, tr, s);
@@ -152,7 +152,7 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
         d.n = L.n;
         d.P = P;
         d.area = L.area64.as<double>();
-        d.tr = L.tr64.as<double4>();
+        d.tr = L.tr64.as<double4_32a>();
         d.nbr = L.nbr.as<int4>();
         d.pst = L.pst.as<int4>();
         d.V = V64.as<double>();
@@ -306,15 +306,23 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
     Program prog;
     auto lvl_count = [&](int m) { return mem[m]->nlev; };
 
-    auto emit_smooth = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
+    auto rows_level = [&](int m, int l) {
+        const LevelStore &Ls = mem[m]->lev[l];
+        return precision == 1 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && mem[m]->nz % 8 == 0;
+    };
+    auto emit_smooth_one = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
         if (ml.empty()) return;
         Op op;
         op.kind = Op::kSmooth;
         op.off = int(items.size());
         op.rho = rho;
         op.max_nz = 0;
+        int nz_items = 0, z_items = 0;
+        op.rows_ok = true;
         for (auto [m, l] : ml) {
+            if (!rows_level(m, l)) op.rows_ok = false;
             MemberState &s = st[m];
+            (s.zero[l] ? z_items : nz_items) += 1;
             push_items(items, base[m] + l, mem[m]->lev[l].ncol, s.cur[l], 1 - s.cur[l], s.zero[l]);
             s.cur[l] ^= 1;
             s.zero[l] = 0;
@@ -326,7 +334,17 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
             }
         }
         op.n = int(items.size()) - op.off;
+        op.zero_mode = z_items == 0 ? 0 : (nz_items == 0 ? 1 : 2);
+        if (op.zero_mode == 2) op.rows_ok = false;
         prog.ops.push_back(op);
+    };
+    // one launch for the levels the row-staged kernel takes, one for the rest,
+    // so that a member's kernel does not depend on the other members
+    auto emit_smooth = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
+        std::vector<std::pair<int, int>> a, b;
+        for (auto ml1 : ml) (rows_level(ml1.first, ml1.second) ? a : b).push_back(ml1);
+        emit_smooth_one(a, rho);
+        emit_smooth_one(b, rho);
     };
     auto emit_memsets = [&](const std::vector<std::pair<int, int>> &ml) {
         for (auto [m, l] : ml) {
@@ -431,7 +449,15 @@ static void run_program(Plan &pl, const Program &prog) {
             case Op::kSmooth: {
                 const bool timed = p0.prof && op.finest;
                 if (timed) p0.prof_mark_begin(s);
-                check_cuda(launch_smooth<T>(s, L, it + op.off, op.n, T(op.rho), op.max_nz), "smooth");
+                if (sizeof(T) == 4 && op.rows_ok)
+                    check_cuda(launch_smooth_rows(s, reinterpret_cast<const Lv<float> *>(L),
+                                                  it + op.off, op.n, float(op.rho), op.max_nz,
+                                                  op.zero_mode, p0.smooth_ctas_per_sm),
+                               "smooth_rows");
+                else
+                    check_cuda(launch_smooth<T>(s, L, it + op.off, op.n, T(op.rho), op.max_nz,
+                                                op.zero_mode),
+                               "smooth");
                 if (timed) p0.prof_mark_end(s, op.bytes);
                 count(pl);
                 break;
@@ -946,8 +972,17 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
         case 0: check_cuda(launch_resid<T>(s, L, it, per, 0, nullptr), "apply"); break;
         case 1: check_cuda(launch_resid<T>(s, L, it, per, 1, nullptr), "residual"); break;
         case 2: {
-            for (int sw = 0; sw < nsweeps; ++sw)
-                check_cuda(launch_smooth<T>(s, L, it + sw * per, per, T(rho), p.nz), "smooth");
+            const LevelStore &Ls = p.lev[level];
+            const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0;
+            for (int sw = 0; sw < nsweeps; ++sw) {
+                if (rows)
+                    check_cuda(launch_smooth_rows(s, reinterpret_cast<const Lv<float> *>(L),
+                                                  it + sw * per, per, float(rho), p.nz, 0,
+                                                  p.smooth_ctas_per_sm),
+                               "smooth_rows");
+                else
+                    check_cuda(launch_smooth<T>(s, L, it + sw * per, per, T(rho), p.nz, 0), "smooth");
+            }
             if (nsweeps & 1)
                 check_cuda(cudaMemcpyAsync(out, tmp.p, nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                            "copy back");

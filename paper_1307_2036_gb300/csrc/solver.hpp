@@ -67,6 +67,8 @@ struct Op {
     int max_nz = 0;           // largest nz among the items
     bool finest = false;      // smooths a finest level (profiled)
     double bytes = 0.0;       // algorithmic bytes of the finest-level work
+    int zero_mode = 0;        // smoother items: 0 none / 1 all start from zero, 2 mixed
+    bool rows_ok = false;     // every level in the op suits the row-staged FP32 smoother
     int member = 0, level = 0, buf = 0;  // kMemset target
 };
 
@@ -133,6 +135,7 @@ struct Problem {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_graph;
     int ev_next = 0, ev_graph_used = 0;
+    int smooth_ctas_per_sm = 0;  // row-staged smoother occupancy cap (0: as many as fit)
     double prof_ms = 0.0, prof_bytes = 0.0;
     long prof_count = 0;
     std::vector<double> ev_free_bytes, ev_graph_bytes;  // bytes per recorded pair
