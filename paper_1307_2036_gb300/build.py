@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libellsolve.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "solver.cu", "geometry.cpp", "server.cpp"]
+SOURCES = ["kernels.cu", "solver.cu", "geometry.cpp", "server.cpp", "noalloc.cu"]
 
 
 def _nvcc():

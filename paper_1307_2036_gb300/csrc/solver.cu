@@ -1005,8 +1005,6 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
 // ===========================================================================
 using namespace ells;
 
-struct ellsolve_s : Problem {};
-
 #define ELLS_GUARD_BEGIN try {
 #define ELLS_GUARD_END                                                   \
     }                                                                    \

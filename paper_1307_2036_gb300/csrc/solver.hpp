@@ -155,3 +155,6 @@ ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
                          std::vector<ellsolve_result> &res);
 
 }  // namespace ells
+
+// The opaque handle of the C ABI is a Problem.
+struct ellsolve_s : ells::Problem {};

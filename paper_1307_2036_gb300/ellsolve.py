@@ -62,6 +62,7 @@ _SIGS = {
     "ellsolve_level_smooth": (_st, [_vp, _i, _i, _vp, _vp, _i, _d]),
     "ellsolve_level_restrict_residual": (_st, [_vp, _i, _i, _vp, _vp, _vp]),
     "ellsolve_level_prolong_add": (_st, [_vp, _i, _i, _vp, _vp]),
+    "ellsolve_level_smooth_noalloc": (_st, [_vp, _i, _i, _vp, _vp, _i, _d]),
     "ellsolve_profile_enable": (_st, [_vp, _i]),
     "ellsolve_profile_read": (_st, [_vp, C.POINTER(_d), C.POINTER(_i), C.POINTER(_d)]),
     "ellsolve_launch_count": (C.c_uint64, [_vp]),
