@@ -873,6 +873,14 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 // Shared-memory budget for the Thomas coefficients of one block.
 constexpr size_t kSmemCap = 227 * 1024;
 
+bool smooth_uses_global_scratch(int max_nz, size_t elem_bytes) {
+    const size_t ring = size_t(kRing) * 6 * kBlk * elem_bytes;
+    const size_t cpb = (size_t(kBlk) * max_nz * elem_bytes + 15) / 16 * 16;
+    return !(elem_bytes == 4 && cpb + ring <= kSmemCap);
+}
+
+bool smooth_rows_fits(int max_nz) { return rows_smem_bytes(max_nz) <= kSmemCap; }
+
 template <typename T, int Z>
 static cudaError_t launch_smooth_z(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
                                    T rho, int max_nz) {

@@ -21,6 +21,12 @@ cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int
 cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                                float rho, int max_nz, int zero_mode, int ctas_per_sm);
 
+// Whether the generic smoother keeps its Thomas coefficients in the level's
+// aux buffer (true) or in shared memory, and whether the row-staged kernel's
+// shared memory fits, for a largest nz of max_nz.
+bool smooth_uses_global_scratch(int max_nz, size_t elem_bytes);
+bool smooth_rows_fits(int max_nz);
+
 // mode 0: aux = A u[in]; mode 1: aux = b - A u[in]; mode 2: only the partial
 // sums of (b - A u[in])^2 into partials[item] (FP64).
 template <typename T>

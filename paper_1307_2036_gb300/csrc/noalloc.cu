@@ -96,7 +96,8 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
                "items");
     const Lv<T> *L = reinterpret_cast<const Lv<T> *>(base);
     const Item *it = reinterpret_cast<const Item *>(base + off_items);
-    const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0;
+    const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0 &&
+                              smooth_rows_fits(p.nz);
     for (int sw = 0; sw < nsweeps; ++sw) {
         const Item *its = it + size_t(sw & 1) * per;
         if (rows)

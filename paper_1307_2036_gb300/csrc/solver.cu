@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -73,77 +74,154 @@ Problem::~Problem() {
     for (auto &e : ev_graph) cudaEventDestroy(e);
 }
 
-void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *rl,
-                    const ellsolve_opts &o, cudaStream_t s) {
-    grid = g;
-    opts = o;
-    omega2 = w2;
-    lambda2 = l2;
-    stream = s;
-    nz = g.nz;
-    r.assign(rl, rl + nz + 1);
-    HostHierarchy H = build_hierarchy(g.kind, g.n, g.mapping, g.box_side, o.coarsest_min,
-                                      o.max_levels);
-    P = H.P;
-    nlev = int(H.levels.size());
-    N = size_t(H.levels[0].ncol) * nz;
+// ---------------------------------------------------------------------------
+// Geometry cache
+// ---------------------------------------------------------------------------
+namespace {
+struct GeoKey {
+    int kind, n, mapping, cmin, maxl;
+    double side;
+    bool operator<(const GeoKey &o) const {
+        if (kind != o.kind) return kind < o.kind;
+        if (n != o.n) return n < o.n;
+        if (mapping != o.mapping) return mapping < o.mapping;
+        if (cmin != o.cmin) return cmin < o.cmin;
+        if (maxl != o.maxl) return maxl < o.maxl;
+        return side < o.side;
+    }
+};
+std::mutex g_geo_mu;
+std::map<GeoKey, std::weak_ptr<const Geometry>> g_geo_cache;
 
-    std::vector<double> V, G;
-    radial_vectors(r.data(), nz, V, G);
-    std::vector<double> gv(nz + 1);
-    for (int k = 0; k <= nz; ++k) gv[k] = w2 * l2 * G[k];
-    std::vector<float> V32(V.begin(), V.end()), g32(gv.begin(), gv.end());
-    upload(V64, V, s);
-    upload(g64, gv, s);
-    upload(this->V32, V32, s);
-    upload(this->g32, g32, s);
+GeoKey geo_key(const ellsolve_grid &g, int coarsest_min, int max_levels) {
+    return GeoKey{g.kind, g.n, g.kind == 1 ? g.mapping : 0, coarsest_min, max_levels,
+                  g.kind == 0 ? g.box_side : 0.0};
+}
+}  // namespace
 
-    const bool need64 = true;                // level 0 always (outer residual, PCG)
-    const bool need32 = o.precision == 1;
-    lev.resize(nlev);
-    h64.resize(nlev);
-    h32.resize(nlev);
-    for (int l = 0; l < nlev; ++l) {
+std::shared_ptr<const Geometry> geometry_for(const ellsolve_grid &g, int coarsest_min,
+                                             int max_levels, cudaStream_t s) {
+    const GeoKey key = geo_key(g, coarsest_min, max_levels);
+    std::lock_guard<std::mutex> lock(g_geo_mu);
+    auto f = g_geo_cache.find(key);
+    if (f != g_geo_cache.end())
+        if (auto sp = f->second.lock()) return sp;
+    HostHierarchy H = build_hierarchy(g.kind, g.n, g.mapping, g.box_side, coarsest_min, max_levels);
+    auto geo = std::make_shared<Geometry>();
+    geo->kind = H.kind;
+    geo->P = H.P;
+    geo->mapping = H.mapping;
+    geo->lev.resize(H.levels.size());
+    for (size_t l = 0; l < H.levels.size(); ++l) {
         const HostLevel &hl = H.levels[l];
-        LevelStore &L = lev[l];
+        LevelGeom &L = geo->lev[l];
         L.n = hl.n;
         L.ncol = int(hl.ncol);
-        const size_t nc = size_t(hl.ncol), nl = nc * nz;
+        const size_t nc = size_t(hl.ncol);
         std::vector<int4> nb(nc), ps(nc);
+        std::vector<double4_32a> tr64(nc);
+        std::vector<float4> tr32(nc);
+        std::vector<float> a32(hl.area.begin(), hl.area.end());
         for (size_t c = 0; c < nc; ++c) {
             nb[c] = make_int4(hl.nbr[4 * c], hl.nbr[4 * c + 1], hl.nbr[4 * c + 2], hl.nbr[4 * c + 3]);
             if (!hl.pst.empty())
                 ps[c] = make_int4(hl.pst[4 * c], hl.pst[4 * c + 1], hl.pst[4 * c + 2], hl.pst[4 * c + 3]);
+            const double *t = &hl.trans[4 * c];
+            tr64[c] = make_double4_32a(t[0], t[1], t[2], t[3]);
+            tr32[c] = make_float4(float(t[0]), float(t[1]), float(t[2]), float(t[3]));
         }
         upload(L.nbr, nb, s);
         if (!hl.pst.empty()) upload(L.pst, ps, s);
-        const bool lev64 = need64 && (l == 0 || o.precision == 0);
-        if (lev64) {
-            std::vector<double4_32a> tr(nc);
-            for (size_t c = 0; c < nc; ++c)
-                tr[c] = make_double4_32a(hl.trans[4 * c], hl.trans[4 * c + 1], hl.trans[4 * c + 2],
-                                     hl.trans[4 * c + 3]);
-            upload(L.area64, hl.area, s);
-            upload(L.tr64, tr, s);
-            if (o.precision == 0) {
-                L.u64[0].alloc(nl * 8);
-                L.u64[1].alloc(nl * 8);
-                L.b64.alloc(nl * 8);
-                L.aux64.alloc(nl * 8);
-            }
+        upload(L.area64, hl.area, s);
+        upload(L.tr64, tr64, s);
+        upload(L.area32, a32, s);
+        upload(L.tr32, tr32, s);
+        geo->bytes += L.nbr.bytes + L.pst.bytes + L.area64.bytes + L.tr64.bytes + L.area32.bytes +
+                      L.tr32.bytes;
+    }
+    std::shared_ptr<const Geometry> out = geo;
+    g_geo_cache[key] = out;
+    return out;
+}
+
+namespace {
+// levels (n, ncol) of the hierarchy a grid gets, without building it
+std::vector<std::pair<int, size_t>> level_sizes(const ellsolve_grid &g, const ellsolve_opts &o) {
+    std::vector<std::pair<int, size_t>> v;
+    const size_t P = g.kind == 0 ? 1 : 6;
+    int m = g.n;
+    for (;;) {
+        v.push_back({m, P * size_t(m) * m});
+        if (m % 2 != 0 || m / 2 < std::max(1, o.coarsest_min)) break;
+        if (o.max_levels > 0 && int(v.size()) >= o.max_levels) break;
+        if (v.size() >= 32) break;
+        m /= 2;
+    }
+    return v;
+}
+}  // namespace
+
+size_t problem_vector_bytes(const ellsolve_grid &g, const ellsolve_opts &o) {
+    size_t t = 0;
+    bool first = true;
+    for (auto [n, nc] : level_sizes(g, o)) {
+        const size_t nl = nc * size_t(g.nz);
+        if (o.precision == 0) t += 4 * nl * 8;
+        else {
+            t += 3 * nl * 4;
+            if (smooth_uses_global_scratch(g.nz, 4)) t += nl * 4;
         }
-        if (need32) {
-            std::vector<float> a32(hl.area.begin(), hl.area.end());
-            std::vector<float4> tr(nc);
-            for (size_t c = 0; c < nc; ++c)
-                tr[c] = make_float4(float(hl.trans[4 * c]), float(hl.trans[4 * c + 1]),
-                                    float(hl.trans[4 * c + 2]), float(hl.trans[4 * c + 3]));
-            upload(L.area32, a32, s);
-            upload(L.tr32, tr, s);
+        (void)n;
+        (void)first;
+        first = false;
+    }
+    return t + size_t(4) * (g.nz + 1) * 8;
+}
+
+size_t geometry_bytes(const ellsolve_grid &g, const ellsolve_opts &o) {
+    size_t t = 0;
+    for (auto [n, nc] : level_sizes(g, o)) t += nc * (16 + 16 + 8 + 32 + 4 + 16);
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Problem set-up
+// ---------------------------------------------------------------------------
+void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *rl,
+                    const ellsolve_opts &o, cudaStream_t s) {
+    grid = g;
+    opts = o;
+    stream = s;
+    nz = g.nz;
+    geom = geometry_for(g, o.coarsest_min, o.max_levels, s);
+    P = geom->P;
+    nlev = int(geom->lev.size());
+    N = size_t(geom->lev[0].ncol) * nz;
+    V64.alloc(nz * 8);
+    g64.alloc((nz + 1) * 8);
+    V32.alloc(nz * 4);
+    g32.alloc((nz + 1) * 4);
+    lev.resize(nlev);
+    h64.resize(nlev);
+    h32.resize(nlev);
+    const bool glob32 = smooth_uses_global_scratch(nz, 4);
+    for (int l = 0; l < nlev; ++l) {
+        const LevelGeom &G = geom->lev[l];
+        LevelStore &L = lev[l];
+        L.geo = &G;
+        L.n = G.n;
+        L.ncol = G.ncol;
+        const size_t nl = size_t(G.ncol) * nz;
+        if (o.precision == 0) {
+            L.u64[0].alloc(nl * 8);
+            L.u64[1].alloc(nl * 8);
+            L.b64.alloc(nl * 8);
+            L.aux64.alloc(nl * 8);
+        } else {
             L.u32[0].alloc(nl * 4);
             L.u32[1].alloc(nl * 4);
             L.b32.alloc(nl * 4);
-            if (size_t(kBlk) * nz * 4 > 200 * 1024) L.aux32.alloc(nl * 4);
+            if (glob32) L.aux32.alloc(nl * 4);
         }
         Lv<double> &d = h64[l];
         std::memset(&d, 0, sizeof(d));
@@ -151,13 +229,12 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
         d.nz = nz;
         d.n = L.n;
         d.P = P;
-        d.area = L.area64.as<double>();
-        d.tr = L.tr64.as<double4_32a>();
-        d.nbr = L.nbr.as<int4>();
-        d.pst = L.pst.as<int4>();
+        d.area = G.area64.as<double>();
+        d.tr = G.tr64.as<double4_32a>();
+        d.nbr = G.nbr.as<int4>();
+        d.pst = G.pst.as<int4>();
         d.V = V64.as<double>();
         d.g = g64.as<double>();
-        d.w2 = w2;
         d.u[0] = L.u64[0].as<double>();
         d.u[1] = L.u64[1].as<double>();
         d.b = L.b64.as<double>();
@@ -168,13 +245,12 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
         e.nz = nz;
         e.n = L.n;
         e.P = P;
-        e.area = L.area32.as<float>();
-        e.tr = L.tr32.as<float4>();
-        e.nbr = L.nbr.as<int4>();
-        e.pst = L.pst.as<int4>();
-        e.V = this->V32.as<float>();
-        e.g = this->g32.as<float>();
-        e.w2 = float(w2);
+        e.area = G.area32.as<float>();
+        e.tr = G.tr32.as<float4>();
+        e.nbr = G.nbr.as<int4>();
+        e.pst = G.pst.as<int4>();
+        e.V = V32.as<float>();
+        e.g = g32.as<float>();
         e.u[0] = L.u32[0].as<float>();
         e.u[1] = L.u32[1].as<float>();
         e.b = L.b32.as<float>();
@@ -183,14 +259,34 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
     check_cuda(cudaHostAlloc(reinterpret_cast<void **>(&pinned), 64 * sizeof(double),
                              cudaHostAllocDefault),
                "cudaHostAlloc");
+    rebind(w2, l2, rl);
+}
+
+void Problem::rebind(double w2, double l2, const double *rl) {
+    omega2 = w2;
+    lambda2 = l2;
+    r.assign(rl, rl + nz + 1);
+    std::vector<double> V, G;
+    radial_vectors(r.data(), nz, V, G);
+    std::vector<double> gv(nz + 1);
+    for (int k = 0; k <= nz; ++k) gv[k] = w2 * l2 * G[k];
+    std::vector<float> V32h(V.begin(), V.end()), g32h(gv.begin(), gv.end());
+    check_cuda(cudaMemcpyAsync(V64.p, V.data(), nz * 8, cudaMemcpyHostToDevice, stream), "V");
+    check_cuda(cudaMemcpyAsync(g64.p, gv.data(), (nz + 1) * 8, cudaMemcpyHostToDevice, stream), "g");
+    check_cuda(cudaMemcpyAsync(V32.p, V32h.data(), nz * 4, cudaMemcpyHostToDevice, stream), "V32");
+    check_cuda(cudaMemcpyAsync(g32.p, g32h.data(), (nz + 1) * 4, cudaMemcpyHostToDevice, stream),
+               "g32");
+    check_cuda(cudaStreamSynchronize(stream), "rebind sync");
+    for (auto &d : h64) d.w2 = w2;
+    for (auto &e : h32) e.w2 = float(w2);
+    plan.reset();  // descriptors changed
 }
 
 size_t Problem::footprint_bytes() const {
-    size_t t = 0;
+    size_t t = V64.bytes + g64.bytes + V32.bytes + g32.bytes;
     for (const auto &L : lev)
-        t += L.area64.bytes + L.tr64.bytes + L.area32.bytes + L.tr32.bytes + L.nbr.bytes +
-             L.pst.bytes + L.u64[0].bytes + L.u64[1].bytes + L.b64.bytes + L.aux64.bytes +
-             L.u32[0].bytes + L.u32[1].bytes + L.b32.bytes + L.aux32.bytes;
+        t += L.u64[0].bytes + L.u64[1].bytes + L.b64.bytes + L.aux64.bytes + L.u32[0].bytes +
+             L.u32[1].bytes + L.b32.bytes + L.aux32.bytes;
     return t;
 }
 
@@ -272,13 +368,15 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
     upload(dfirst, first_dev, s);
     partials.alloc(size_t(std::max(outer_n, 1)) * sizeof(double));
     norms.alloc(size_t(M) * 4 * sizeof(double));
-    scales.alloc(size_t(M) * sizeof(double));
+    scales.alloc(size_t(2) * M * sizeof(double));
     std::vector<double> cnt(M), ones(M, 1.0);
     for (int m = 0; m < M; ++m) cnt[m] = double(mem[m]->N);
     upload(counts, cnt, s);
     stage_active.assign(M, 1);
     upload(active, stage_active, s);
-    check_cuda(cudaMemcpyAsync(scales.p, ones.data(), M * sizeof(double), cudaMemcpyHostToDevice, s),
+    std::vector<double> ones2(2 * M, 1.0);
+    check_cuda(cudaMemcpyAsync(scales.p, ones2.data(), 2 * M * sizeof(double),
+                               cudaMemcpyHostToDevice, s),
                "scales");
     check_cuda(cudaStreamSynchronize(s), "plan sync");
     host_norms.assign(M, 0.0);
@@ -308,7 +406,8 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
 
     auto rows_level = [&](int m, int l) {
         const LevelStore &Ls = mem[m]->lev[l];
-        return precision == 1 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && mem[m]->nz % 8 == 0;
+        return precision == 1 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && mem[m]->nz % 8 == 0 &&
+               smooth_rows_fits(mem[m]->nz);
     };
     auto emit_smooth_one = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
         if (ml.empty()) return;
@@ -627,26 +726,34 @@ static ellsolve_status solve_mg64(Problem &p, const double *f, double *x, double
     return finish(rel, iters, rtol, stag, res, secs);
 }
 
+// ---------------------------------------------------------------------------
 // Mixed precision: FP32 V-cycles on the FP64 residual (iterative refinement).
-// The outer descriptors of each member point at its x and pointwise f.
-static void ir_outer_descs(Plan &pl, const std::vector<const double *> &f,
-                           const std::vector<double *> &x) {
+// The inner right-hand side of member m is r * s_m with s_m a power of two
+// near sqrt(N)/||r||: scaling by a power of two is exact, so the result does
+// not depend on when s_m was chosen (alone or in a batch) -- it only keeps the
+// FP32 values away from underflow.  The update reads the scale the residual was
+// formed with (scale_cur); the new residual is formed with scale_next.
+// ---------------------------------------------------------------------------
+static double pow2_scale(double norm, size_t N) {
+    if (!(norm > 0) || !std::isfinite(norm)) return 1.0;
+    return std::ldexp(1.0, -std::ilogb(norm / std::sqrt(double(N))));
+}
+
+// Outer descriptors: member m's finest FP64 level with u[0] = x_m, b = f_m.
+void ir_bind(Plan &pl, const std::vector<MemberRun *> &run) {
     const int M = int(pl.mem.size());
-    std::vector<Lv<double>> o64(M);
-    std::vector<Lv<float>> f32(M);
+    pl.stage64.resize(M);
+    pl.stage32.resize(M);
     for (int m = 0; m < M; ++m) {
-        o64[m] = pl.mem[m]->h64[0];
-        o64[m].u[0] = x[m];
-        o64[m].u[1] = nullptr;
-        o64[m].b = const_cast<double *>(f[m]);
-        f32[m] = pl.mem[m]->h32[0];
+        pl.stage64[m] = pl.mem[m]->h64[0];
+        pl.stage64[m].u[0] = run[m]->x;
+        pl.stage64[m].u[1] = nullptr;
+        pl.stage64[m].b = const_cast<double *>(run[m]->f);
+        pl.stage32[m] = pl.mem[m]->h32[0];
     }
     cudaStream_t s = pl.mem[0]->stream;
     if (pl.outer64.bytes != M * sizeof(Lv<double>)) pl.outer64.alloc(M * sizeof(Lv<double>));
     if (pl.fine32.bytes != M * sizeof(Lv<float>)) pl.fine32.alloc(M * sizeof(Lv<float>));
-    // the host staging copy must outlive the asynchronous copy: keep it in the plan
-    pl.stage64 = o64;
-    pl.stage32 = f32;
     check_cuda(cudaMemcpyAsync(pl.outer64.p, pl.stage64.data(), M * sizeof(Lv<double>),
                                cudaMemcpyHostToDevice, s),
                "outer desc");
@@ -654,27 +761,70 @@ static void ir_outer_descs(Plan &pl, const std::vector<const double *> &f,
                                cudaMemcpyHostToDevice, s),
                "fine desc");
     check_cuda(cudaStreamSynchronize(s), "desc sync");
-    if (pl.gexec) {
-        // descriptors changed in place; the graph reads them by address, so it stays valid
-    }
 }
 
-static void ir_residual_norm(Plan &pl, int op, int x_is_zero = 0) {
-    cudaStream_t s = pl.mem[0]->stream;
-    const Item *it = pl.ditems.as<Item>();
+static void ir_push_state(Plan &pl, const std::vector<MemberRun *> &run) {
     const int M = int(pl.mem.size());
+    pl.stage_scales.resize(2 * M);
+    pl.stage_active.resize(M);
+    for (int m = 0; m < M; ++m) {
+        pl.stage_scales[m] = run[m]->scale_cur;
+        pl.stage_scales[M + m] = run[m]->scale_next;
+        pl.stage_active[m] = run[m]->active ? 1 : 0;
+    }
+    cudaStream_t s = pl.mem[0]->stream;
+    check_cuda(cudaMemcpyAsync(pl.scales.p, pl.stage_scales.data(), 2 * M * sizeof(double),
+                               cudaMemcpyHostToDevice, s),
+               "scales");
+    check_cuda(cudaMemcpyAsync(pl.active.p, pl.stage_active.data(), M * sizeof(int),
+                               cudaMemcpyHostToDevice, s),
+               "active");
+}
+
+// FP64 residual of members [m0, m1) formed with scale_next, and its norm
+static void ir_residual_norm(Plan &pl, int m0, int m1, int x_is_zero) {
+    cudaStream_t s = pl.mem[0]->stream;
+    const int M = int(pl.mem.size());
+    const int i0 = pl.outer_first[m0], i1 = pl.outer_first[m1];
     check_cuda(launch_ir_residual(s, pl.outer64.as<Lv<double>>(), pl.fine32.as<Lv<float>>(),
-                                  it + pl.outer_off, pl.outer_n, pl.scales.as<double>(),
-                                  pl.partials.as<double>(), x_is_zero),
+                                  pl.ditems.as<Item>() + pl.outer_off + i0, i1 - i0,
+                                  pl.scales.as<double>() + M, pl.partials.as<double>() + i0,
+                                  x_is_zero),
                "ir_residual");
-    check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>(), M,
-                               pl.norms.as<double>(), op, op == 2 ? pl.scales.as<double>() : nullptr,
-                               pl.counts.as<double>()),
+    check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>() + m0, m1 - m0,
+                               pl.norms.as<double>() + m0, 1, nullptr, nullptr),
                "finalize");
     count(pl, 2);
 }
 
-// one refinement step: inner V-cycles on r32, x += e / scale, new residual and norm
+// Start members [m0, m1): x = 0 unless keep_x, ||r||, scales, first residual.
+void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep_x) {
+    if (m1 <= m0) return;
+    cudaStream_t s = pl.mem[0]->stream;
+    pl.sync_items();
+    for (int m = m0; m < m1; ++m) {
+        MemberRun &r = *run[m];
+        if (!keep_x) check_cuda(cudaMemsetAsync(r.x, 0, pl.mem[m]->N * 8, s), "zero x");
+        r.scale_cur = r.scale_next = 1.0;
+        r.active = true;
+        r.iters = 0;
+        r.hist.assign(1, 1.0);
+    }
+    ir_push_state(pl, run);
+    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
+    read_norms(pl, int(pl.mem.size()));
+    for (int m = m0; m < m1; ++m) {
+        MemberRun &r = *run[m];
+        r.bnorm = pl.host_norms[m];
+        r.rel = std::isfinite(r.bnorm) ? (r.bnorm > 0 ? 1.0 : 0.0) : r.bnorm;
+        if (!(r.bnorm > 0) || !std::isfinite(r.bnorm)) r.active = false;
+        r.scale_cur = r.scale_next = pow2_scale(r.bnorm, pl.mem[m]->N);
+    }
+    ir_push_state(pl, run);
+    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
+}
+
+// one refinement step: inner V-cycles on r32, x += e / scale_cur, new residual
 static void ir_step(Plan &pl) {
     cudaStream_t s = pl.mem[0]->stream;
     const int M = int(pl.mem.size());
@@ -694,7 +844,7 @@ static void ir_step(Plan &pl) {
                                 pl.active.as<int>()),
                "ir_update");
     count(pl);
-    ir_residual_norm(pl, 1);
+    ir_residual_norm(pl, 0, M, 0);
 }
 
 static void ir_step_graph(Plan &pl) {
@@ -752,6 +902,34 @@ static void ir_step_graph(Plan &pl) {
     count(pl, pl.graph_launches);
 }
 
+// One refinement step for every member, then the per-member bookkeeping:
+// convergence (rtol, maxit, stagnation, non-finite) and the next scale.
+void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph) {
+    const int M = int(pl.mem.size());
+    Problem &p0 = *pl.mem[0];
+    const int cycles = std::max(1, p0.opts.inner_cycles);
+    ir_push_state(pl, run);
+    if (use_graph) ir_step_graph(pl);
+    else ir_step(pl);
+    read_norms(pl, M);
+    p0.prof_collect(use_graph);
+    for (int m = 0; m < M; ++m) {
+        MemberRun &r = *run[m];
+        if (!r.active) continue;
+        r.iters += cycles;
+        r.rel = pl.host_norms[m] / r.bnorm;
+        r.hist.push_back(r.rel);
+        r.scale_cur = r.scale_next;
+        r.scale_next = pow2_scale(pl.host_norms[m], pl.mem[m]->N);
+        if (!(r.rel > r.rtol) || !std::isfinite(r.rel) || r.iters >= r.maxit || stagnated(r.hist))
+            r.active = false;
+    }
+}
+
+ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res) {
+    return finish(r.rel, r.iters, r.rtol, false, res, secs);
+}
+
 ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
                          const std::vector<double *> &x, double rtol, int maxit,
                          std::vector<ellsolve_result> &res) {
@@ -759,70 +937,29 @@ ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
     Problem &p0 = *pl.mem[0];
     cudaStream_t s = p0.stream;
     auto t0 = std::chrono::steady_clock::now();
-    for (int m = 0; m < M; ++m)
-        check_cuda(cudaMemsetAsync(x[m], 0, pl.mem[m]->N * 8, s), "zero x");
-    ir_outer_descs(pl, f, x);
-    pl.sync_items();
-    std::vector<double> ones(M, 1.0);
-    pl.stage_scales = ones;
-    check_cuda(cudaMemcpyAsync(pl.scales.p, pl.stage_scales.data(), M * sizeof(double),
-                               cudaMemcpyHostToDevice, s),
-               "scale reset");
-    pl.stage_active.assign(M, 1);
-    check_cuda(cudaMemcpyAsync(pl.active.p, pl.stage_active.data(), M * sizeof(int),
-                               cudaMemcpyHostToDevice, s),
-               "active reset");
-    // ||b|| (x = 0 so the residual is b) and the FP32 scaling sqrt(N)/||b||
-    ir_residual_norm(pl, 2, 1);
-    read_norms(pl, M);
-    std::vector<double> bnorm = pl.host_norms;
-    // residual with the final scaling (x = 0 still)
-    ir_residual_norm(pl, 1, 1);
-    std::vector<std::vector<double>> hist(M, std::vector<double>{1.0});
-    std::vector<int> iters(M, 0);
-    std::vector<char> active(M, 1);
-    std::vector<double> rel(M, 1.0);
-    for (int m = 0; m < M; ++m)
-        if (!(bnorm[m] > 0)) {
-            active[m] = 0;
-            rel[m] = 0.0;
-        }
-    const int cycles = std::max(1, p0.opts.inner_cycles);
-    int step = 0;
-    bool any = std::any_of(active.begin(), active.end(), [](char a) { return a != 0; });
-    while (any && step * cycles < maxit) {
-        if (p0.opts.use_graph) ir_step_graph(pl);
-        else ir_step(pl);
-        ++step;
-        read_norms(pl, M);
-        p0.prof_collect(p0.opts.use_graph != 0);
-        for (int m = 0; m < M; ++m) {
-            if (!active[m]) continue;
-            iters[m] = step * cycles;
-            rel[m] = pl.host_norms[m] / bnorm[m];
-            hist[m].push_back(rel[m]);
-            if (!(rel[m] > rtol) || !std::isfinite(rel[m]) || stagnated(hist[m])) active[m] = 0;
-        }
-        // A finished member rides along in the launches but its solution is
-        // no longer updated, so it ends exactly where it would have alone.
-        bool changed = false;
-        for (int m = 0; m < M; ++m)
-            if (pl.stage_active[m] != int(active[m])) {
-                pl.stage_active[m] = active[m];
-                changed = true;
-            }
-        if (changed)
-            check_cuda(cudaMemcpyAsync(pl.active.p, pl.stage_active.data(), M * sizeof(int),
-                                       cudaMemcpyHostToDevice, s),
-                       "active");
-        any = std::any_of(active.begin(), active.end(), [](char a) { return a != 0; });
+    std::vector<MemberRun> runs(M);
+    std::vector<MemberRun *> run(M);
+    for (int m = 0; m < M; ++m) {
+        runs[m].f = f[m];
+        runs[m].x = x[m];
+        runs[m].rtol = rtol;
+        runs[m].maxit = maxit;
+        run[m] = &runs[m];
     }
+    ir_bind(pl, run);
+    ir_start(pl, run, 0, M, false);
+    auto any = [&]() {
+        return std::any_of(runs.begin(), runs.end(), [](const MemberRun &r) { return r.active; });
+    };
+    if (maxit <= 0)
+        for (auto &r : runs) r.active = false;
+    while (any()) ir_advance(pl, run, p0.opts.use_graph != 0);
     check_cuda(cudaStreamSynchronize(s), "solve sync");
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     res.resize(M);
     ellsolve_status worst = ELLSOLVE_OK;
     for (int m = 0; m < M; ++m) {
-        ellsolve_status st = finish(rel[m], iters[m], rtol, false, &res[m], secs);
+        ellsolve_status st = run_result(runs[m], secs, &res[m]);
         if (st < 0 || (st > worst && worst >= 0)) worst = st;
     }
     return worst;
@@ -973,7 +1110,8 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
         case 1: check_cuda(launch_resid<T>(s, L, it, per, 1, nullptr), "residual"); break;
         case 2: {
             const LevelStore &Ls = p.lev[level];
-            const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0;
+            const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0 &&
+                              smooth_rows_fits(p.nz);
             for (int sw = 0; sw < nsweeps; ++sw) {
                 if (rows)
                     check_cuda(launch_smooth_rows(s, reinterpret_cast<const Lv<float> *>(L),
@@ -1109,19 +1247,15 @@ ellsolve_status ellsolve_vcycle(ellsolve_t h, const void *f, void *u) {
         check_cuda(cudaMemcpyAsync(u, h->h64[0].u[h->fine_cur], h->N * 8, cudaMemcpyDeviceToDevice, s),
                    "out");
     } else {
-        std::vector<const double *> fv{static_cast<const double *>(f)};
-        std::vector<double *> xv{static_cast<double *>(u)};
-        ir_outer_descs(pl, fv, xv);
-        pl.sync_items();
-        // scaling from ||b||: residual of x = 0 would need a zero x, so scale by the current residual
-        std::vector<double> ones(1, 1.0);
-        pl.stage_scales = ones;
-        check_cuda(cudaMemcpyAsync(pl.scales.p, pl.stage_scales.data(), sizeof(double),
-                                   cudaMemcpyHostToDevice, s),
-                   "scale");
-        ir_residual_norm(pl, 2);
-        ir_residual_norm(pl, 1);
-        ir_step(pl);
+        MemberRun r;
+        r.f = static_cast<const double *>(f);
+        r.x = static_cast<double *>(u);
+        r.rtol = 0.0;
+        r.maxit = 1;
+        std::vector<MemberRun *> run{&r};
+        ir_bind(pl, run);
+        ir_start(pl, run, 0, 1, true);  // residual of the given iterate
+        if (r.active) ir_advance(pl, run, false);
     }
     check_cuda(cudaStreamSynchronize(s), "vcycle sync");
     return ELLSOLVE_OK;

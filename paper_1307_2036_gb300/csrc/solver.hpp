@@ -51,13 +51,33 @@ struct DevBuf {
     T *as() const { return static_cast<T *>(p); }
 };
 
-// Device storage of one multigrid level of one problem.
-struct LevelStore {
+// Device geometry of one level: column metrics and connectivity (FP64 and FP32).
+struct LevelGeom {
     int n = 0, ncol = 0;
     DevBuf area64, tr64, area32, tr32, nbr, pst;
+};
+
+// The hierarchy of one grid; shared by every problem on that grid and kept
+// resident while any of them lives (process-wide cache keyed by the grid).
+struct Geometry {
+    int kind = 0, P = 1, mapping = 0;
+    std::vector<LevelGeom> lev;
+    size_t bytes = 0;
+};
+std::shared_ptr<const Geometry> geometry_for(const ellsolve_grid &g, int coarsest_min,
+                                             int max_levels, cudaStream_t s);
+
+// Device vectors of one multigrid level of one problem.
+struct LevelStore {
+    int n = 0, ncol = 0;
+    const LevelGeom *geo = nullptr;
     DevBuf u64[2], b64, aux64;
     DevBuf u32[2], b32, aux32;
 };
+
+// Device bytes a problem needs beyond its (shared) geometry.
+size_t problem_vector_bytes(const ellsolve_grid &g, const ellsolve_opts &o);
+size_t geometry_bytes(const ellsolve_grid &g, const ellsolve_opts &o);
 
 // One launch of a V-cycle program.
 struct Op {
@@ -121,6 +141,7 @@ struct Problem {
     size_t N = 0;
     cudaStream_t stream = nullptr;      // the caller's stream: all work is ordered on it
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    std::shared_ptr<const Geometry> geom;
     std::vector<LevelStore> lev;
     DevBuf V64, g64, V32, g32;
     std::vector<Lv<double>> h64;
@@ -143,12 +164,32 @@ struct Problem {
     ~Problem();
     void build(const ellsolve_grid &g, double w2, double l2, const double *r_levels,
                const ellsolve_opts &o, cudaStream_t s);
+    // new omega^2, lambda^2 and radial levels on the same grid and nz (reuse)
+    void rebind(double w2, double l2, const double *r_levels);
     Plan &single_plan();
     size_t footprint_bytes() const;
     void prof_mark_begin(cudaStream_t s);
     void prof_mark_end(cudaStream_t s, double bytes);
     void prof_collect(bool graph_replayed);
 };
+
+// Per-member state of an iterative-refinement solve.
+struct MemberRun {
+    const double *f = nullptr;  // pointwise right-hand side (device)
+    double *x = nullptr;        // solution (device)
+    double rtol = 0.0;
+    int maxit = 0;
+    double bnorm = 0.0, rel = 1.0;
+    int iters = 0;
+    std::vector<double> hist;
+    bool active = true;
+    double scale_cur = 1.0, scale_next = 1.0;
+};
+
+void ir_bind(Plan &pl, const std::vector<MemberRun *> &run);
+void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep_x);
+void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph);
+ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res);
 
 ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
                          const std::vector<double *> &x, double rtol, int maxit,

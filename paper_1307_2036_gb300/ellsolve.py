@@ -205,3 +205,43 @@ def solve_batch(solvers, rhs, xs, rtol=1e-8, maxit=50):
     res = (ellsolve_result * n)()
     st = check(_lib.ellsolve_solve_batch(hs, n, rp, xp, float(rtol), int(maxit), res), "solve_batch")
     return st, list(res)
+
+
+class Server:
+    """Continuous-batching request server (ellsolve_server_*).  The caller keeps
+    each request's rhs and x tensors alive and leaves them untouched until its
+    poll returns a final status; rhs must be fully written before submit."""
+
+    def __init__(self, hbm_budget_bytes, max_slots, stream=None):
+        self.stream = _current_stream() if stream is None else stream
+        h = C.c_void_p()
+        check(_lib.ellsolve_server_create(C.c_size_t(int(hbm_budget_bytes)), int(max_slots),
+                                          C.c_void_p(self.stream), C.byref(h)),
+              "ellsolve_server_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ellsolve_server_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def submit(self, kind, n, nz, r_levels, omega2, lambda2, f, x, rtol=1e-5, maxit=50,
+               mapping=0, box_side=None):
+        import math
+        g = ellsolve_grid(kind=kind, n=n, nz=nz,
+                          box_side=2 * math.pi if box_side is None else box_side, mapping=mapping)
+        r = (C.c_double * (nz + 1))(*[float(v) for v in r_levels])
+        t = C.c_uint64()
+        check(_lib.ellsolve_submit(self.h, C.byref(g), float(omega2), float(lambda2), r, _ptr(f),
+                                   _ptr(x), float(rtol), int(maxit), C.byref(t)), "ellsolve_submit")
+        return t.value
+
+    def poll(self, ticket, timeout_us=-1):
+        """Returns (status, result); status PENDING if not finished in time."""
+        res = ellsolve_result()
+        st = _lib.ellsolve_poll(self.h, C.c_uint64(ticket), int(timeout_us), C.byref(res))
+        if st < 0 and st != ERR_NONFINITE:
+            raise EllsolveError(st, "ellsolve_poll")
+        return st, res

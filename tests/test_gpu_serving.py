@@ -1,0 +1,124 @@
+"""Serving: continuous batching through ellsolve_server_create / submit / poll.
+
+Requests of mixed grids, sizes and parameters are submitted together to a
+server with fewer slots than requests, so later requests are admitted while
+earlier ones are on the GPU and all admitted requests advance in the same
+batched launches.  Each result must equal the same solve done alone (the
+refinement scales by powers of two and every member's reductions run over its
+own fixed blocks, so the equality is exact).  Failure paths are driven from the
+host: an oversized request, a poll that times out, a right-hand side with a NaN.
+"""
+import numpy as np
+import pytest
+
+from paper_1307_2036_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # kind, n, nz, graded, omega2, lambda2, rtol
+    (1, 8, 16, True, 0.01, 1.0, 1e-8),
+    (0, 24, 12, True, 0.05, 4.0, 1e-5),
+    (1, 12, 32, True, 0.002, 0.25, 1e-10),
+    (1, 6, 8, False, 0.03, 9.0, 1e-8),
+    (0, 16, 16, False, 0.01, 1.0, 1e-10),
+    (1, 16, 16, True, 0.1, 25.0, 1e-6),
+]
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1307_2036_gb300 import ellsolve  # noqa: F401  (fails loudly if unbuilt)
+    return torch
+
+
+def rhs(torch, kind, n, nz, member):
+    shape = (nz, 1 if kind == 0 else 6, n, n)
+    return torch.tensor(inputs.uniform_pm1(shape, member=member), device="cuda")
+
+
+def solve_alone(torch, spec, f):
+    from paper_1307_2036_gb300 import ellsolve
+    kind, n, nz, graded, w2, l2, rtol = spec
+    sv = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=graded), w2, l2,
+                         precision=1)
+    x = torch.zeros_like(f)
+    st, res = sv.solve(f, x, rtol=rtol, maxit=60)
+    torch.cuda.synchronize()
+    return st, res, x
+
+
+@pytest.mark.parametrize("slots", [2, 6])
+def test_served_results_equal_solves_alone(torch_mod, slots):
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    fs = [rhs(torch, s[0], s[1], s[2], 40 + i) for i, s in enumerate(SPECS)]
+    alone = [solve_alone(torch, s, f) for s, f in zip(SPECS, fs)]
+    torch.cuda.synchronize()
+    srv = ellsolve.Server(hbm_budget_bytes=4 << 30, max_slots=slots)
+    xs = [torch.full_like(f, 7.0) for f in fs]  # overwritten by the server
+    torch.cuda.synchronize()
+    tickets = []
+    for s, f, x in zip(SPECS, fs, xs):
+        kind, n, nz, graded, w2, l2, rtol = s
+        tickets.append(srv.submit(kind, n, nz, inputs.radial_levels(nz, graded=graded), w2, l2, f, x,
+                                  rtol=rtol, maxit=60))
+    for t, (st_a, res_a, x_a), x in zip(tickets, alone, xs):
+        st, res = srv.poll(t, timeout_us=-1)
+        assert st == st_a == ellsolve.OK
+        assert res.iterations == res_a.iterations
+        assert res.rel_residual == res_a.rel_residual
+        assert torch.equal(x, x_a)
+        assert res.seconds > 0
+    srv.close()
+
+
+def test_capacity_and_unknown_ticket(torch_mod):
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    srv = ellsolve.Server(hbm_budget_bytes=1 << 20, max_slots=4)  # 1 MiB
+    f = torch.zeros(16 * 6 * 32 * 32, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(f)
+    with pytest.raises(ellsolve.EllsolveError) as e:
+        srv.submit(1, 32, 16, inputs.radial_levels(16), 0.01, 1.0, f, x)
+    assert e.value.status == ellsolve.ERR_CAPACITY
+    with pytest.raises(ellsolve.EllsolveError):
+        srv.poll(12345, timeout_us=0)
+    srv.close()
+
+
+def test_poll_timeout_then_completion(torch_mod):
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    srv = ellsolve.Server(hbm_budget_bytes=8 << 30, max_slots=1)
+    spec = (1, 96, 64, True, 0.01, 1.0, 1e-10)
+    f = rhs(torch, 1, 96, 64, 7)
+    x = torch.zeros_like(f)
+    torch.cuda.synchronize()
+    t = srv.submit(1, 96, 64, inputs.radial_levels(64, graded=True), 0.01, 1.0, f, x, rtol=1e-10)
+    st, _ = srv.poll(t, timeout_us=0)
+    assert st in (ellsolve.PENDING, ellsolve.OK)
+    st, res = srv.poll(t, timeout_us=-1)
+    assert st == ellsolve.OK and res.rel_residual <= 1e-10
+    srv.close()
+
+
+def test_nonfinite_rhs_reported(torch_mod):
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    srv = ellsolve.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    good = rhs(torch, 0, 16, 8, 1)
+    bad = good.clone()
+    bad.view(-1)[123] = float("nan")
+    xg, xb = torch.zeros_like(good), torch.zeros_like(bad)
+    torch.cuda.synchronize()
+    r = inputs.radial_levels(8)
+    tb = srv.submit(0, 16, 8, r, 0.01, 1.0, bad, xb, rtol=1e-8)
+    tg = srv.submit(0, 16, 8, r, 0.01, 1.0, good, xg, rtol=1e-8)
+    st_b, _ = srv.poll(tb, timeout_us=-1)
+    st_g, res_g = srv.poll(tg, timeout_us=-1)
+    assert st_b == ellsolve.ERR_NONFINITE
+    assert st_g == ellsolve.OK and res_g.rel_residual <= 1e-8
+    srv.close()
