@@ -6,12 +6,12 @@
  *     -omega^2 (Laplace_2d u + lambda^2 r^-2 d/dr (r^2 du/dr)) + u = f     (Eq. ModelEquation)
  *
  * on the shell 1 <= r <= 1 + H over a doubly periodic box or the cubed sphere
- * (Eqs. x1x2_1, x1x2_2), homogeneous Neumann at the bottom and top (Sec. 2),
+ * (Eqs. x1x2_1, x1x2_2), homogeneous Neumann at the bottom and top (Sec. 3),
  * discretised with cell-centred finite volumes and a 7-point stencil
- * (Sec. 2.1).  Solvers: the tensor-product geometric multigrid V-cycle
+ * (Sec. 3.1).  Solvers: the tensor-product geometric multigrid V-cycle
  * (Algorithm 1; horizontal-only coarsening, vertical line relaxation,
- * Sec. 4.1.3 and 5.2.1) and CG preconditioned by vertical line relaxation
- * (Algorithm PCG, Sec. 5.2.2).
+ * Sec. 4.3.1 and 5.2.1) and CG preconditioned by vertical line relaxation
+ * (Algorithm PCG, Sec. 6.2.2).
  *
  * Conventions for every call below:
  *  - Vectors are device buffers of doubles in the layout [nz][P][n][n]:
@@ -110,7 +110,7 @@ void ellsolve_destroy(ellsolve_t h);
 size_t ellsolve_size(ellsolve_t h);
 int ellsolve_num_levels(ellsolve_t h);
 
-/* y = A x on the finest level (Sec. 2.1 stencil), FP64 device buffers. */
+/* y = A x on the finest level (Sec. 3.1 stencil), FP64 device buffers. */
 ellsolve_status ellsolve_apply(ellsolve_t h, const void *x_dev, void *y_dev);
 
 /* One multigrid V-cycle (Algorithm 1) in place on u_dev for the pointwise
@@ -143,11 +143,11 @@ ellsolve_status ellsolve_level_apply(ellsolve_t h, int level, int fp32, const vo
 /* r = b - A_level u */
 ellsolve_status ellsolve_level_residual(ellsolve_t h, int level, int fp32, const void *b,
                                         const void *u, void *r);
-/* nsweeps damped block-Jacobi vertical line relaxation sweeps (Sec. 3.2,
+/* nsweeps damped block-Jacobi vertical line relaxation sweeps (Sec. 4.2,
  * Algorithm Thomas per column), u <- u + rho Dtilde^{-1}(b - A u), in place. */
 ellsolve_status ellsolve_level_smooth(ellsolve_t h, int level, int fp32, const void *b, void *u,
                                       int nsweeps, double rho);
-/* b_c = R (b - A u) on level+1: residual summed over the 2 x 2 children (Sec. 5.2.1). */
+/* b_c = R (b - A u) on level+1: residual summed over the 2 x 2 children (Sec. 6.2.1). */
 ellsolve_status ellsolve_level_restrict_residual(ellsolve_t h, int level, int fp32,
                                                  const void *b, const void *u, void *b_c);
 /* u += P u_c from level+1 (bilinear or constant per opts.prolong). */

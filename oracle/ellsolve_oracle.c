@@ -2,14 +2,14 @@
  * ellsolve oracle -- plain, slow, FP64 CPU reference (TEST INFRASTRUCTURE ONLY).
  *
  * Follows Mueller & Scheichl, arXiv:1307.2036:
- *   model equation            Eq. ModelEquation (Sec. 2), Neumann top/bottom
- *   cubed-sphere grid         Eqs. x1x2_1, x1x2_2 (Sec. 2.1)
- *   vertical grading          Eq. VerticalGrading (Sec. 2.1)
- *   cell-centred FV, 7 points Sec. 2.1 (two-point face fluxes)
- *   tensor-product structure  Sec. 4.1.3
- *   block (line) relaxation   Sec. 3.2, Eq. BlockRBSOR with the Jacobi ordering
+ *   model equation            Eq. ModelEquation (Sec. 3), Neumann top/bottom
+ *   cubed-sphere grid         Eqs. x1x2_1, x1x2_2 (Sec. 3.1)
+ *   vertical grading          Eq. VerticalGrading (Sec. 3.1)
+ *   cell-centred FV, 7 points Sec. 3.1 (two-point face fluxes)
+ *   tensor-product structure  Sec. 4.3.1
+ *   block (line) relaxation   Sec. 4.2, Eq. BlockRBSOR with the Jacobi ordering
  *   Thomas algorithm          Algorithm Thomas (appendix)
- *   V-cycle                   Algorithm 1 (Sec. 3.3), components of Sec. 5.2.1
+ *   V-cycle                   Algorithm 1 (Sec. 4.3), components of Sec. 6.2.1
  *   PCG                       Algorithm PCG (appendix), sign of the residual
  *                             update read as r_K = r_{K-1} - alpha q_{K-1}
  *
@@ -399,7 +399,7 @@ void og_thomas_excess(int n, const double *delta, const double *up, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Block (vertical line) relaxation, Sec. 3.2: Dtilde_P is the tridiagonal    */
+/* Block (vertical line) relaxation, Sec. 4.2: Dtilde_P is the tridiagonal    */
 /* block of A coupling the cells of column P (the full diagonal and the       */
 /* vertical off-diagonals).  One damped block-Jacobi sweep is                 */
 /*   u <- u + rho Dtilde^{-1} (b - A u).                                      */
@@ -462,7 +462,7 @@ void og_line_precond(const og_grid *g, int lev, const double *r, double *z)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Intergrid transfers (Sec. 5.2.1): horizontal cell average for the          */
+/* Intergrid transfers (Sec. 6.2.1): horizontal cell average for the          */
 /* restriction -- in the volume-integrated form the coarse right-hand side    */
 /* is the sum of the four children -- and linear interpolation for the        */
 /* prolongation, with the vertical index unchanged.                           */

@@ -3,8 +3,8 @@
  * equation of Mueller & Scheichl, "Massively parallel solvers for elliptic PDEs
  * in Numerical Weather- and Climate Prediction" (arXiv:1307.2036), and of the
  * two solvers studied there: the tensor-product geometric multigrid V-cycle
- * (Algorithm 1, Sec. 4.1.3 and 5.2.1) and CG preconditioned by vertical line
- * relaxation (Algorithm PCG, Sec. 3.1 and 5.2.2).
+ * (Algorithm 1, Sec. 4.3.1 and 5.2.1) and CG preconditioned by vertical line
+ * relaxation (Algorithm PCG, Sec. 4.1 and 5.2.2).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline of the benchmark may load this code.  It shares no code, header,
@@ -46,7 +46,7 @@ void og_get_face_lengths(const og_grid *g, int lev, double *ell, double *dist);
 void og_get_radial(const og_grid *g, double *V, double *G);
 void og_volumes(const og_grid *g, int lev, double *vol);
 
-/* Operator (Sec. 2.1, 7-point cell-centred finite volumes). */
+/* Operator (Sec. 3.1, 7-point cell-centred finite volumes). */
 void og_apply(const og_grid *g, int lev, const double *u, double *y);
 void og_residual(const og_grid *g, int lev, const double *b, const double *u, double *r);
 void og_assemble_dense(const og_grid *g, int lev, double *M);

@@ -1,5 +1,5 @@
-// Grid hierarchy for the periodic box and the cubed sphere (Sec. 2.1,
-// Eqs. x1x2_1 / x1x2_2), with rediscretised coarse levels (Sec. 4.1.4: the
+// Grid hierarchy for the periodic box and the cubed sphere (Sec. 3.1,
+// Eqs. x1x2_1 / x1x2_2), with rediscretised coarse levels (Sec. 4.3.2: the
 // coarse operators come from discretising on the coarse grid).
 #include "geometry.hpp"
 

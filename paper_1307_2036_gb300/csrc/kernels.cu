@@ -3,11 +3,11 @@
 // Layout: every level vector is [nz][ncol], column index fastest, so a warp of
 // 32 threads -- one vertical column each -- touches 32 consecutive values at
 // every level k: each vertical sweep is a sequence of coalesced 128-byte rows.
-// The matrix is never stored (Sec. 5.2.1): a column keeps its area and four
+// The matrix is never stored (Sec. 6.2.1): a column keeps its area and four
 // face transmissibilities in registers, the radial vectors V, g are shared by
 // all columns, and the stencil is recomputed on the fly.
 //
-// Operator (finite-volume form of Eq. ModelEquation, Sec. 2.1):
+// Operator (finite-volume form of Eq. ModelEquation, Sec. 3.1):
 //   (Au)_{c,k} = A_c V_k u + w2 V_k sum_q T_q (u - u_q)
 //              + A_c [g_{k+1} (u - u_{k+1}) + g_k (u - u_{k-1})],  g = w2 lambda^2 G
 // written with differences so that FP32 keeps the small mass term accurate
@@ -110,7 +110,7 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ---------------------------------------------------------------------------
-// Line smoother (Sec. 3.2, Eq. BlockRBSOR with the Jacobi ordering; Algorithm
+// Line smoother (Sec. 4.2, Eq. BlockRBSOR with the Jacobi ordering; Algorithm
 // Thomas per column): u_out = u_in + rho Dtilde^{-1} (b - A u_in).
 // Forward sweep k = 0..nz-1: residual on the fly and the elimination; the
 // eliminated right-hand side f'_k is parked in u_out (it stays in L2 until the
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kBlk) k_smooth_rows(const Lv<float> *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Residual / apply (Sec. 2.1 stencil).
+// Residual / apply (Sec. 3.1 stencil).
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlk) k_resid(const Lv<T> *__restrict__ L,
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kBlk) k_resid(const Lv<T> *__restrict__ L,
 }
 
 // ---------------------------------------------------------------------------
-// Residual fused with the restriction (Sec. 5.2.1: cell average; in volume-
+// Residual fused with the restriction (Sec. 6.2.1: cell average; in volume-
 // integrated form the coarse right-hand side is the sum over the 2x2 children).
 // One thread per coarse column.
 // ---------------------------------------------------------------------------
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Prolongation and coarse-grid correction (Algorithm 1; Sec. 5.2.1 linear
+// Prolongation and coarse-grid correction (Algorithm 1; Sec. 6.2.1 linear
 // interpolation): cell-centred bilinear weights 9/16, 3/16, 3/16, 1/16; where
 // three cells meet at a cube corner, 1/2, 1/4, 1/4.
 // ---------------------------------------------------------------------------

@@ -3,7 +3,7 @@
 tests/golden/table1_parameter_space.txt holds Table 1 of arXiv:1307.2036.
 omega^2 and lambda^2 follow from Eq. omega2lambda2 and the time step; the
 anisotropy beta = lambda^2 (dx/dz)^2 follows from the typical spacing
-dx = 2 pi R / (4 nx) (Sec. 2.1.2) and the level spacing of Eq. VerticalGrading,
+dx = 2 pi R / (4 nx) (Sec. 3.1.2) and the level spacing of Eq. VerticalGrading,
 which the input generator's radial_levels() produces.  Every printed entry is
 reproduced to 1% except beta_top of the nx = 512 row, printed as 4.69 where the
 paper's own formulas give 46.9 (read as a misprint by a factor of ten).
@@ -47,6 +47,6 @@ def test_anisotropy_from_vertical_grading():
 
 
 def test_horizontal_coupling_value():
-    """Sec. 2.1.2: nx = 256, dt = 10 min gives C_horiz = alpha^2 (c_h dt / dx)^2 ~ 17.8."""
+    """Sec. 3.1.2: nx = 256, dt = 10 min gives C_horiz = alpha^2 (c_h dt / dx)^2 ~ 17.8."""
     dx = 2 * np.pi * R_EARTH / (4 * 256)
     assert abs(ALPHA ** 2 * (C_H * 600.0 / dx) ** 2 - 17.8) < 0.1

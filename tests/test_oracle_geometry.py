@@ -9,7 +9,7 @@ Each check uses a fact that the oracle's code does not itself compute:
   * two cells are neighbours exactly when they share a face: the end points of
     the face seen from either side coincide on the sphere;
   * rediscretised coarse cells are the unions of their four children.
-Grid: Eqs. x1x2_1/x1x2_2 (cubed sphere), Sec. 2.1; periodic box of side 2 pi.
+Grid: Eqs. x1x2_1/x1x2_2 (cubed sphere), Sec. 3.1; periodic box of side 2 pi.
 """
 import numpy as np
 import pytest

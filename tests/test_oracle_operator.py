@@ -1,8 +1,8 @@
 """Pins of the oracle's discrete operator (CPU only).
 
 Operator: Eq. ModelEquation integrated over each cell with two-point face
-fluxes (Sec. 2.1), Neumann at r = 1 and r = 1 + H; tensor-product form of
-Sec. 4.1.3.  Checks that do not reuse the oracle's formula:
+fluxes (Sec. 3.1), Neumann at r = 1 and r = 1 + H; tensor-product form of
+Sec. 4.3.1.  Checks that do not reuse the oracle's formula:
   * A 1 = cell volumes (a constant has no flux on any face);
   * symmetry and positive definiteness of the assembled matrix;
   * the assembled matrix and the matrix-free apply agree (two code paths);

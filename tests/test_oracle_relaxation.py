@@ -7,10 +7,10 @@ transfers (CPU only).
     must not;
   * one line-relaxation sweep equals u + rho * Dtilde^{-1}(b - A u), with
     Dtilde cut out of the assembled matrix as its vertical tridiagonal blocks
-    (Sec. 3.2) and solved densely;
+    (Sec. 4.2) and solved densely;
   * restriction conserves the integrated residual; prolongation reproduces
     constants everywhere (cube corners included) and linear fields inside a
-    panel (Sec. 5.2.1: cell average / linear interpolation).
+    panel (Sec. 6.2.1: cell average / linear interpolation).
 """
 import numpy as np
 import pytest

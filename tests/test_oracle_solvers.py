@@ -5,7 +5,7 @@
   * the V-cycle with zero initial guess is a linear map of the right-hand side;
   * PCG's recursively updated residual equals the true b - A u;
   * the tensor-product multigrid converges with a factor that does not drift
-    with n_z or lambda (Sec. 4.1.3, Boerm & Hiptmair; Table 6's finding that the
+    with n_z or lambda (Sec. 4.3.1, Boerm & Hiptmair; Table 6's finding that the
     iteration count is independent of lambda^2), and the iteration count to a
     1e-5 reduction does not grow with the horizontal resolution (Table 3).
 """
@@ -70,7 +70,7 @@ def test_mg_factor_robust_in_nz_and_lambda(oracle_mod):
 
 
 def test_mg_iterations_do_not_grow_with_n(oracle_mod):
-    """Weak scaling as in Sec. 5.1: the time step shrinks with the grid spacing,
+    """Weak scaling as in Sec. 7.1: the time step shrinks with the grid spacing,
     so omega^2 n^2 (the horizontal coupling C_horiz, Eq. Choriz) stays fixed.
     The number of V-cycles to a 1e-5 reduction then stays fixed (Table 3)."""
     its = []
