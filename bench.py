@@ -284,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
-KERNEL_REV = "smooth-v6-rcpapprox"
+KERNEL_REV = "smooth-v7-pairs-f32x2"
 
 
 def main():

@@ -20,6 +20,10 @@ cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int
 // caps the resident CTAs per SM (through the shared-memory request).
 cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                                float rho, int max_nz, int zero_mode, int ctas_per_sm);
+// Same sweep with two columns per thread and packed FP32x2 arithmetic (64-thread CTAs
+// over the same 128-column items).
+cudaError_t launch_smooth_rows2(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                                float rho, int max_nz, int zero_mode, int ctas_per_sm);
 
 // Whether the generic smoother keeps its Thomas coefficients in the level's
 // aux buffer (true) or in shared memory, and whether the row-staged kernel's

@@ -96,17 +96,9 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
                "items");
     const Lv<T> *L = reinterpret_cast<const Lv<T> *>(base);
     const Item *it = reinterpret_cast<const Item *>(base + off_items);
-    const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0 &&
-                              smooth_rows_fits(p.nz);
-    for (int sw = 0; sw < nsweeps; ++sw) {
-        const Item *its = it + size_t(sw & 1) * per;
-        if (rows)
-            check_cuda(launch_smooth_rows(s, reinterpret_cast<const Lv<float> *>(L), its, per,
-                                          float(rho), p.nz, 0, p.smooth_ctas_per_sm),
-                       "smooth_rows");
-        else
-            check_cuda(launch_smooth<T>(s, L, its, per, T(rho), p.nz, 0), "smooth");
-    }
+    const bool rows = sizeof(T) == 4 && rows_eligible(p, level);
+    for (int sw = 0; sw < nsweeps; ++sw)
+        launch_smoother<T>(p, s, L, it + size_t(sw & 1) * per, per, rho, p.nz, 0, rows);
     if (nsweeps & 1)
         check_cuda(cudaMemcpyAsync(u, d.u[1], nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                    "copy back");

@@ -404,11 +404,7 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
     Program prog;
     auto lvl_count = [&](int m) { return mem[m]->nlev; };
 
-    auto rows_level = [&](int m, int l) {
-        const LevelStore &Ls = mem[m]->lev[l];
-        return precision == 1 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && mem[m]->nz % 8 == 0 &&
-               smooth_rows_fits(mem[m]->nz);
-    };
+    auto rows_level = [&](int m, int l) { return precision == 1 && rows_eligible(*mem[m], l); };
     auto emit_smooth_one = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
         if (ml.empty()) return;
         Op op;
@@ -525,6 +521,32 @@ void Plan::sync_items() {
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
+bool rows_eligible(const Problem &p, int level) {
+    const LevelStore &Ls = p.lev[level];
+    return Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0 && smooth_rows_fits(p.nz);
+}
+
+template <typename T>
+void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
+                     double rho, int max_nz, int zero_mode, bool rows_ok) {
+    if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
+        const Lv<float> *Lf = reinterpret_cast<const Lv<float> *>(L);
+        if (p.smooth_variant == 2)
+            check_cuda(launch_smooth_rows2(s, Lf, it, n, float(rho), max_nz, zero_mode,
+                                           p.smooth_ctas_per_sm),
+                       "smooth_rows2");
+        else
+            check_cuda(launch_smooth_rows(s, Lf, it, n, float(rho), max_nz, zero_mode,
+                                          p.smooth_ctas_per_sm),
+                       "smooth_rows");
+    } else {
+        check_cuda(launch_smooth<T>(s, L, it, n, T(rho), max_nz, zero_mode), "smooth");
+    }
+}
+template void launch_smoother<float>(const Problem &, cudaStream_t, const Lv<float> *,
+                                     const Item *, int, double, int, int, bool);
+template void launch_smoother<double>(const Problem &, cudaStream_t, const Lv<double> *,
+                                      const Item *, int, double, int, int, bool);
 static void count(Plan &pl, int n = 1) {
     for (Problem *p : pl.mem) p->launches += uint64_t(n);
 }
@@ -548,15 +570,8 @@ static void run_program(Plan &pl, const Program &prog) {
             case Op::kSmooth: {
                 const bool timed = p0.prof && op.finest;
                 if (timed) p0.prof_mark_begin(s);
-                if (sizeof(T) == 4 && op.rows_ok)
-                    check_cuda(launch_smooth_rows(s, reinterpret_cast<const Lv<float> *>(L),
-                                                  it + op.off, op.n, float(op.rho), op.max_nz,
-                                                  op.zero_mode, p0.smooth_ctas_per_sm),
-                               "smooth_rows");
-                else
-                    check_cuda(launch_smooth<T>(s, L, it + op.off, op.n, T(op.rho), op.max_nz,
-                                                op.zero_mode),
-                               "smooth");
+                launch_smoother<T>(p0, s, L, it + op.off, op.n, op.rho, op.max_nz, op.zero_mode,
+                                   op.rows_ok);
                 if (timed) p0.prof_mark_end(s, op.bytes);
                 count(pl);
                 break;
@@ -1109,18 +1124,9 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
         case 0: check_cuda(launch_resid<T>(s, L, it, per, 0, nullptr), "apply"); break;
         case 1: check_cuda(launch_resid<T>(s, L, it, per, 1, nullptr), "residual"); break;
         case 2: {
-            const LevelStore &Ls = p.lev[level];
-            const bool rows = sizeof(T) == 4 && Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0 &&
-                              smooth_rows_fits(p.nz);
-            for (int sw = 0; sw < nsweeps; ++sw) {
-                if (rows)
-                    check_cuda(launch_smooth_rows(s, reinterpret_cast<const Lv<float> *>(L),
-                                                  it + sw * per, per, float(rho), p.nz, 0,
-                                                  p.smooth_ctas_per_sm),
-                               "smooth_rows");
-                else
-                    check_cuda(launch_smooth<T>(s, L, it + sw * per, per, T(rho), p.nz, 0), "smooth");
-            }
+            const bool rows = sizeof(T) == 4 && rows_eligible(p, level);
+            for (int sw = 0; sw < nsweeps; ++sw)
+                launch_smoother<T>(p, s, L, it + sw * per, per, rho, p.nz, 0, rows);
             if (nsweeps & 1)
                 check_cuda(cudaMemcpyAsync(out, tmp.p, nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                            "copy back");

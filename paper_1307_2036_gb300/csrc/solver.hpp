@@ -156,7 +156,8 @@ struct Problem {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_graph;
     int ev_next = 0, ev_graph_used = 0;
-    int smooth_ctas_per_sm = 0;  // row-staged smoother occupancy cap (0: as many as fit)
+    int smooth_ctas_per_sm = 4;  // row-staged smoother occupancy cap (0: as many as fit)
+    int smooth_variant = 2;      // FP32 row-staged smoother: 2 two columns/thread, 1 one
     double prof_ms = 0.0, prof_bytes = 0.0;
     long prof_count = 0;
     std::vector<double> ev_free_bytes, ev_graph_bytes;  // bytes per recorded pair
@@ -190,6 +191,13 @@ void ir_bind(Plan &pl, const std::vector<MemberRun *> &run);
 void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep_x);
 void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph);
 ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res);
+
+// One line-smoother launch: the row-staged FP32 kernels where `rows_ok`, else
+// the generic kernel.
+template <typename T>
+void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
+                     double rho, int max_nz, int zero_mode, bool rows_ok);
+bool rows_eligible(const Problem &p, int level);
 
 ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
                          const std::vector<double *> &x, double rtol, int maxit,
