@@ -824,11 +824,22 @@ __global__ void __launch_bounds__(kBlk) k_resid(const Lv<T> *__restrict__ L,
 // ---------------------------------------------------------------------------
 // Residual fused with the restriction (Sec. 6.2.1: cell average; in volume-
 // integrated form the coarse right-hand side is the sum over the 2x2 children).
-// One thread per coarse column.
+// One thread per coarse column.  Per level the thread needs the four
+// children's u_{k+1} and b_k and the eight neighbours of the 2x2 block across
+// its outer faces (taken from the neighbour table, so panel edges need no
+// special case); the neighbours inside the block are the children themselves.
+// These 16 values are fetched kRR levels ahead by per-thread cp.async copies
+// into a shared-memory ring.
 // ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ constexpr int restrict_ring() { return sizeof(T) == 4 ? 8 : 4; }
+
 template <typename T>
 __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict__ L,
                                                          const Item *__restrict__ items) {
+    constexpr int R = restrict_ring<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *ring = reinterpret_cast<T *>(smem_raw) + threadIdx.x;  // ring[slot][16][kBlk]
     const Item it = items[blockIdx.x];
     const Lv<T> &d = L[it.lv];
     const Lv<T> &dc = L[it.lv + 1];
@@ -837,6 +848,7 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
     if (C >= ncc) return;
     const int nz = d.nz, nf = d.n, ncn = dc.n, nc = d.ncol;
     const int I = C % ncn, t = C / ncn, J = t % ncn, p = t / ncn;
+    // children 0: (2I, 2J), 1: (2I+1, 2J), 2: (2I, 2J+1), 3: (2I+1, 2J+1)
     const int f0 = (p * nf + 2 * J) * nf + 2 * I;
     const int fc[4] = {f0, f0 + 1, f0 + nf, f0 + nf + 1};
     const T *__restrict__ u = d.u[it.in];
@@ -845,35 +857,83 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
     const T *__restrict__ g = d.g;
     T *__restrict__ bc = dc.b;
     Column<T> col[4];
-    T um[4], u0[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) col[q] = load_column(d, fc[q]);
+    // outer neighbours: W of 0 and 2, E of 1 and 3, S of 0 and 1, N of 2 and 3
+    const int ext[8] = {col[0].nb.x, col[2].nb.x, col[1].nb.y, col[3].nb.y,
+                        col[0].nb.z, col[1].nb.z, col[2].nb.w, col[3].nb.w};
+    const size_t snc = size_t(nc);
+    auto issue = [&](int k) {
+        T *sl = ring + (k % R) * 16 * kBlk;
+        const bool ok = k < nz, ok1 = k + 1 < nz;
+        const size_t o = ok ? size_t(k) * snc : 0, o1 = ok1 ? size_t(k + 1) * snc : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cp_async(sl + q * kBlk, u + o1 + fc[q], ok1);
+            cp_async(sl + (4 + q) * kBlk, b + o + fc[q], ok);
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) cp_async(sl + (8 + e) * kBlk, u + o + ext[e], ok);
+        cp_async_commit();
+    };
+#pragma unroll 1
+    for (int k = 0; k < R - 1; ++k) issue(k);
+    T u0[4], um[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        col[q] = load_column(d, fc[q]);
-        um[q] = T(0);
         u0[q] = __ldg(u + fc[q]);
+        um[q] = T(0);
     }
     T gk = __ldg(g);
+#pragma unroll 1
     for (int k = 0; k < nz; ++k) {
-        const size_t o = size_t(k) * nc;
+        cp_async_wait<R - 2>();
+        const T *sl = ring + (k % R) * 16 * kBlk;
+        T up[4], bk[4], ex[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            up[q] = sl[q * kBlk];
+            bk[q] = sl[(4 + q) * kBlk];
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ex[e] = sl[(8 + e) * kBlk];
+        issue(k + R - 1);
         const T Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
+        // neighbours per child: W, E, S, N
+        const T nw[4] = {ex[0], u0[0], ex[1], u0[2]};
+        const T ne[4] = {u0[1], ex[2], u0[3], ex[3]};
+        const T ns[4] = {ex[4], ex[5], u0[0], u0[1]};
+        const T nn[4] = {u0[2], u0[3], ex[6], ex[7]};
         T sum = T(0);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const T up = (k + 1 < nz) ? __ldg(u + o + nc + fc[q]) : T(0);
-            sum += __ldg(b + o + fc[q]) - stencil(col[q], u + o, u0[q], um[q], up, Vk, gk, gk1);
-            um[q] = u0[q];
-            u0[q] = up;
+            const Column<T> &cq = col[q];
+            const T x = u0[q];
+            const T horiz = (cq.t0 * (x - nw[q]) + cq.t1 * (x - ne[q])) +
+                            (cq.t2 * (x - ns[q]) + cq.t3 * (x - nn[q]));
+            const T vert = gk1 * (x - up[q]) + gk * (x - um[q]);
+            sum += bk[q] - (cq.A * (Vk * x) + Vk * horiz + cq.A * vert);
         }
         bc[size_t(k) * ncc + C] = sum;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            um[q] = u0[q];
+            u0[q] = up[q];
+        }
         gk = gk1;
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
 // Prolongation and coarse-grid correction (Algorithm 1; Sec. 6.2.1 linear
 // interpolation): cell-centred bilinear weights 9/16, 3/16, 3/16, 1/16; where
-// three cells meet at a cube corner, 1/2, 1/4, 1/4.
+// three cells meet at a cube corner, 1/2, 1/4, 1/4.  The loads of kPB levels
+// are issued before their arithmetic and stores, so each thread keeps 5 kPB
+// loads in flight.
 // ---------------------------------------------------------------------------
+constexpr int kPB = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ L,
                                                       const Item *__restrict__ items, int mode) {
@@ -885,21 +945,31 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
     if (f >= nc) return;
     const int nz = d.nz;
     const int4 s = d.pst[f];
+    const bool corner = s.w < 0;
+    const int sw = corner ? s.x : s.w;
     const T *__restrict__ uc = dc.u[it.in];
     T *__restrict__ uf = d.u[it.out];
-#pragma unroll 4
-    for (int k = 0; k < nz; ++k) {
-        const T *row = uc + size_t(k) * ncc;
-        T e;
-        if (mode == 1) {
-            e = __ldg(row + s.x);
-        } else if (s.w >= 0) {
-            e = (T(9) * __ldg(row + s.x) + T(3) * __ldg(row + s.y) + T(3) * __ldg(row + s.z) +
-                 __ldg(row + s.w)) * T(0.0625);
-        } else {
-            e = (T(2) * __ldg(row + s.x) + __ldg(row + s.y) + __ldg(row + s.z)) * T(0.25);
+    for (int k0 = 0; k0 < nz; k0 += kPB) {
+        T cx[kPB], cy[kPB], cz[kPB], cw[kPB], fv[kPB];
+#pragma unroll
+        for (int j = 0; j < kPB; ++j) {
+            const int k = k0 + j < nz ? k0 + j : nz - 1;
+            const T *row = uc + size_t(k) * ncc;
+            cx[j] = __ldg(row + s.x);
+            cy[j] = __ldg(row + s.y);
+            cz[j] = __ldg(row + s.z);
+            cw[j] = __ldg(row + sw);
+            fv[j] = uf[size_t(k) * nc + f];
         }
-        uf[size_t(k) * nc + f] += e;
+#pragma unroll
+        for (int j = 0; j < kPB; ++j) {
+            if (k0 + j >= nz) break;
+            T e;
+            if (mode == 1) e = cx[j];
+            else if (!corner) e = (T(9) * cx[j] + T(3) * cy[j] + T(3) * cz[j] + cw[j]) * T(0.0625);
+            else e = (T(2) * cx[j] + cy[j] + cz[j]) * T(0.25);
+            uf[size_t(k0 + j) * nc + f] = fv[j] + e;
+        }
     }
 }
 
@@ -927,14 +997,25 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         const double sc = scale[it.lv];
         const Column<double> col = load_column(d, c);
         double um = 0.0, u0 = XZERO ? 0.0 : __ldg(x + c), up = 0.0, gk = __ldg(g);
+        // FP64 is the scarce unit here: the mass and horizontal terms are formed
+        // as V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding ~eps C_horiz
+        // relative to the mass term, far below the FP64 attainable residual);
+        // the large vertical couplings keep the difference form.
 #pragma unroll 2
         for (int k = 0; k < nz; ++k) {
             const size_t o = size_t(k) * nc;
             const double Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
-            double r = col.A * (Vk * __ldg(f + o + c));
+            double r = (col.A * Vk) * __ldg(f + o + c);
             if (!XZERO) {
                 up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
-                r -= stencil(col, x + o, u0, um, up, Vk, gk, gk1);
+                const double *row = x + o;
+                double hm = col.s * u0;
+                hm = fma(-col.t0, __ldg(row + col.nb.x), hm);
+                hm = fma(-col.t1, __ldg(row + col.nb.y), hm);
+                hm = fma(-col.t2, __ldg(row + col.nb.z), hm);
+                hm = fma(-col.t3, __ldg(row + col.nb.w), hm);
+                const double vert = fma(gk, u0 - um, gk1 * (u0 - up));
+                r -= fma(col.A, vert, Vk * hm);
             }
             r32[o + c] = float(r * sc);
             acc += r * r;
@@ -1247,7 +1328,10 @@ cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int 
 template <typename T>
 cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems) {
     if (nitems <= 0) return cudaSuccess;
-    k_restrict_resid<T><<<nitems, kBlk, 0, s>>>(L, items);
+    const size_t bytes = size_t(restrict_ring<T>()) * 16 * kBlk * sizeof(T);
+    cudaError_t e = set_smem(k_restrict_resid<T>, bytes);
+    if (e != cudaSuccess) return e;
+    k_restrict_resid<T><<<nitems, kBlk, bytes, s>>>(L, items);
     return cudaGetLastError();
 }
 
