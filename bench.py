@@ -171,7 +171,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sv = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=graded), w2, l2,
-                             precision=1, use_graph=1, stream=stream.cuda_stream)
+                             precision=1, use_graph=1, inner_cycles=args.inner_cycles,
+                             stream=stream.cuda_stream)
         f_host = torch.from_numpy(rhs_for(kind, n, nz, rhs_kind, member=rank)).pin_memory()
         f = f_host.to("cuda", non_blocking=True)
         x = torch.zeros_like(f)
@@ -264,6 +265,7 @@ def run_ours(args, rank, world, local_rank):
             "workload": args.workload, "grid": ("cubed sphere 6x" if kind == 1 else "box ") +
             f"{n}x{n}", "nz": nz, "unknowns": N, "omega2": w2, "lambda": l2 ** 0.5,
             "solver": "FP32 V-cycle (2/2 line-Jacobi, rho 0.8) in FP64 refinement, CUDA graph",
+            "inner_cycles": args.inner_cycles,
             "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
             "final_rel_residual": final_rel, "time_to_rtol_ms": ms / args.steps,
             "l2_policy": "inputs larger than L2 (FP32 hierarchy %.1f GB)" % (N * 16 / 3 * 4 / 1e9)},
@@ -295,6 +297,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sphere512")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--inner-cycles", type=int, default=2,
+                    help="FP32 V-cycles per FP64 refinement step")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -994,19 +994,23 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         const double *__restrict__ V = d.V;
         const double *__restrict__ g = d.g;
         float *__restrict__ r32 = L32[it.lv].b;
-        const double sc = scale[it.lv];
+        const float sc = float(scale[it.lv]);  // a power of two: exact in FP32
         const Column<double> col = load_column(d, c);
         double um = 0.0, u0 = XZERO ? 0.0 : __ldg(x + c), up = 0.0, gk = __ldg(g);
+        float colsum = 0.f;  // this column's sum of r^2 (only steers the stopping test)
         // FP64 is the scarce unit here: the mass and horizontal terms are formed
         // as V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding ~eps C_horiz
         // relative to the mass term, far below the FP64 attainable residual);
         // the large vertical couplings keep the difference form.
+        //   r = A (V_k f - vert) - V_k hm
 #pragma unroll 2
         for (int k = 0; k < nz; ++k) {
             const size_t o = size_t(k) * nc;
             const double Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
-            double r = (col.A * Vk) * __ldg(f + o + c);
-            if (!XZERO) {
+            double r;
+            if (XZERO) {
+                r = col.A * (Vk * __ldg(f + o + c));
+            } else {
                 up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
                 const double *row = x + o;
                 double hm = col.s * u0;
@@ -1015,14 +1019,16 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                 hm = fma(-col.t2, __ldg(row + col.nb.z), hm);
                 hm = fma(-col.t3, __ldg(row + col.nb.w), hm);
                 const double vert = fma(gk, u0 - um, gk1 * (u0 - up));
-                r -= fma(col.A, vert, Vk * hm);
+                r = fma(-Vk, hm, col.A * fma(Vk, __ldg(f + o + c), -vert));
             }
-            r32[o + c] = float(r * sc);
-            acc += r * r;
+            const float rf = float(r);
+            r32[o + c] = rf * sc;
+            colsum = fmaf(rf, rf, colsum);
             um = u0;
             u0 = up;
             gk = gk1;
         }
+        acc = double(colsum);
     }
     const double t = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;

@@ -1178,7 +1178,7 @@ void ellsolve_default_opts(ellsolve_opts *o) {
     o->coarsest_min = 4;
     o->max_levels = 0;
     o->prolong = 0;
-    o->inner_cycles = 1;
+    o->inner_cycles = 2;
     o->use_graph = 1;
 }
 
