@@ -179,6 +179,7 @@ def run_ours(args, rank, world, local_rank):
         x_host = torch.empty_like(f_host).pin_memory()
     stream.synchronize()
     N = sv.N
+    tuned_ctas, tuned_ms = sv.autotune()
 
     def solve():
         st, res = sv.solve(f, x, rtol=rtol, maxit=60)
@@ -256,6 +257,12 @@ def run_ours(args, rank, world, local_rank):
         if tinfo.get("workload") == args.workload and tinfo.get("kernel_rev") == KERNEL_REV:
             traffic = tinfo.get("dram_bytes_per_launch")
     cpu_rate, cpu_s, cpu_desc = oracle_rate(ORACLE_SAMPLE, 1) if not args.no_cpu else (None, 0, "")
+    extras = {}
+    if not args.no_extras:
+        del sv
+        torch.cuda.empty_cache()
+        extras["ensemble"] = run_ensemble(torch, stream)
+        extras["serving"] = run_serving(torch, stream, args.serve_requests)
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns*V-cycles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -266,6 +273,7 @@ def run_ours(args, rank, world, local_rank):
             f"{n}x{n}", "nz": nz, "unknowns": N, "omega2": w2, "lambda": l2 ** 0.5,
             "solver": "FP32 V-cycle (2/2 line-Jacobi, rho 0.8) in FP64 refinement, CUDA graph",
             "inner_cycles": args.inner_cycles,
+            "autotuned_smoother_ctas_per_sm": tuned_ctas,
             "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
             "final_rel_residual": final_rel, "time_to_rtol_ms": ms / args.steps,
             "l2_policy": "inputs larger than L2 (FP32 hierarchy %.1f GB)" % (N * 16 / 3 * 4 / 1e9)},
@@ -280,9 +288,135 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_ensemble(torch, stream, members=32, n=128, nz=64, rtol=1e-8, reps=3):
+    """Config 4: `members` independent cubed-sphere problems 6 x n^2 x nz with
+    per-member omega^2 (log-uniform [1e-3, 1e-1]) and lambda (uniform [0.5, 5]),
+    uniform right-hand sides; one batched mixed-precision solve (one launch per
+    kernel and level over all members) against the same solves done one after
+    another in plain FP64 multigrid."""
+    from paper_1307_2036_gb300 import ellsolve, inputs
+    w2s, lams = inputs.member_params(members)
+    r = inputs.radial_levels(nz, graded=True)
+    with torch.cuda.stream(stream):
+        sv = [ellsolve.Solver(1, n, nz, r, float(w2s[m]), float(lams[m]) ** 2, precision=1,
+                              stream=stream.cuda_stream) for m in range(members)]
+        sv[0].autotune()
+        fs = [torch.tensor(inputs.uniform_pm1(sv[0].shape(), member=m), device="cuda")
+              for m in range(members)]
+        xs = [torch.zeros_like(f) for f in fs]
+    stream.synchronize()
+    st, res = ellsolve.solve_batch(sv, fs, xs, rtol=rtol, maxit=60)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        st, res = ellsolve.solve_batch(sv, fs, xs, rtol=rtol, maxit=60)
+    e1.record(stream)
+    stream.synchronize()
+    batched_s = e0.elapsed_time(e1) / 1e3 / reps
+    worst = max(x.rel_residual for x in res)
+    cycles = [x.iterations for x in res]
+    # plain FP64, one member after another
+    with torch.cuda.stream(stream):
+        p64 = [ellsolve.Solver(1, n, nz, r, float(w2s[m]), float(lams[m]) ** 2, precision=0,
+                               stream=stream.cuda_stream) for m in range(members)]
+        x64 = torch.zeros_like(fs[0])
+    p64[0].solve(fs[0], x64, rtol=rtol, maxit=100)  # warm-up
+    stream.synchronize()
+    e0.record(stream)
+    it64 = []
+    for m in range(members):
+        _, r64 = p64[m].solve(fs[m], x64, rtol=rtol, maxit=100)
+        it64.append(r64.iterations)
+    e1.record(stream)
+    stream.synchronize()
+    seq_s = e0.elapsed_time(e1) / 1e3
+    return {"workload": f"{members} members, cubed sphere 6x{n}x{n}x{nz}, rtol {rtol}",
+            "batched_mixed_solves_per_s": members / batched_s,
+            "sequential_fp64_solves_per_s": members / seq_s,
+            "speedup": seq_s / batched_s,
+            "batched_vcycles_per_member": [min(cycles), max(cycles)],
+            "fp64_vcycles_per_member": [min(it64), max(it64)],
+            "worst_rel_residual": worst}
+
+
+def run_serving(torch, stream, count, rate=200.0, budget=96 << 30, slots=16):
+    """Config 5 (bounded sample of `count` requests): Poisson arrivals at `rate`
+    per second, n in {48, 96, 192, 384}, nz in {32, 64, 128}, tol in {1e-5,
+    1e-10}, omega^2 and lambda as in config 4.  Requests go through the
+    continuous-batching server; latency is submit -> completion as the library
+    measures it.  Baseline: plain FP64 multigrid one request at a time in FIFO
+    order, service times measured on the first requests and queued against the
+    same arrivals."""
+    import numpy as np
+
+    from paper_1307_2036_gb300 import ellsolve, inputs
+    req = inputs.request_stream(count, rate=rate)
+    shapes = {}
+    with torch.cuda.stream(stream):
+        for i in range(count):
+            key = (int(req["n"][i]), int(req["nz"][i]))
+            if key not in shapes:
+                shapes[key] = torch.tensor(
+                    inputs.uniform_pm1((key[1], 6, key[0], key[0]), member=1000 + len(shapes)),
+                    device="cuda")
+        xs = [torch.zeros_like(shapes[(int(req["n"][i]), int(req["nz"][i]))]) for i in range(count)]
+    stream.synchronize()
+    srv = ellsolve.Server(budget, slots, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(count):
+        due = t0 + float(req["arrival"][i])
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        n, nz = int(req["n"][i]), int(req["nz"][i])
+        tickets.append(srv.submit(1, n, nz, inputs.radial_levels(nz, graded=True),
+                                  float(req["omega2"][i]), float(req["lam"][i]) ** 2,
+                                  shapes[(n, nz)], xs[i], rtol=float(req["tol"][i]), maxit=80))
+    lat, counts = [], {"ok": 0, "not_converged": 0, "error": 0}
+    for t in tickets:
+        st, res = srv.poll(t, timeout_us=-1)
+        lat.append(res.seconds)
+        counts["ok" if st == ellsolve.OK else
+               "not_converged" if st == ellsolve.NOT_CONVERGED else "error"] += 1
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    # FIFO plain-FP64 baseline on the first requests
+    nb = min(count, 24)
+    svc = []
+    for i in range(nb):
+        n, nz = int(req["n"][i]), int(req["nz"][i])
+        with torch.cuda.stream(stream):
+            p = ellsolve.Solver(1, n, nz, inputs.radial_levels(nz, graded=True),
+                                float(req["omega2"][i]), float(req["lam"][i]) ** 2, precision=0,
+                                stream=stream.cuda_stream)
+        stream.synchronize()
+        a = time.perf_counter()
+        p.solve(shapes[(n, nz)], xs[i], rtol=float(req["tol"][i]), maxit=100)
+        stream.synchronize()
+        svc.append(time.perf_counter() - a)
+        del p
+    done, base = 0.0, []
+    for i in range(nb):
+        start = max(float(req["arrival"][i]), done)
+        done = start + svc[i]
+        base.append(done - float(req["arrival"][i]))
+    base = np.array(base)
+    return {"workload": f"{count} requests, Poisson {rate:g}/s, n in 48..384, nz in 32..128, "
+                        f"tol 1e-5/1e-10; server {slots} slots, {budget >> 30} GiB",
+            "solves_per_s": count / wall, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "status_counts": counts,
+            "note": "not_converged: 1e-10 requests whose FP64 attainable residual is above 1e-10",
+            "fp64_fifo_baseline": {"requests": nb, "solves_per_s": nb / float(np.sum(svc)),
+                                   "p50_latency_s": float(np.percentile(base, 50)),
+                                   "p99_latency_s": float(np.percentile(base, 99))}}
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
@@ -297,6 +431,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sphere512")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests in the bounded serving sample")
     ap.add_argument("--inner-cycles", type=int, default=2,
                     help="FP32 V-cycles per FP64 refinement step")
     args = ap.parse_args()

@@ -190,6 +190,16 @@ ellsolve_status ellsolve_profile_read(ellsolve_t h, double *smoother_ms_total, i
 /* number of kernel launches the library issued on this handle so far */
 uint64_t ellsolve_launch_count(ellsolve_t h);
 
+/* ---- autotuning ----
+ * Times the FP32 line smoother on the handle's finest level for each candidate
+ * number of resident CTAs per SM (the occupancy cap bounds the L2 working set
+ * of the back substitution) and keeps the fastest for later solves on this
+ * handle and for batches led by it.  The choice changes no result (same
+ * arithmetic, different scheduling).  Uses the handle's own FP32 buffers as
+ * scratch: call it between solves.  precision 1 only.  out_ctas / out_ms
+ * (nullable) receive the chosen cap and its time per sweep. */
+ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms);
+
 /* ---- serving: continuous batching of independent solves ----
  * A server owns one CUDA stream's worth of work; submitted requests are admitted
  * while their device footprint fits hbm_budget_bytes and a slot is free, and

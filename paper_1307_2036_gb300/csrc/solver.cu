@@ -1391,4 +1391,57 @@ ellsolve_status ellsolve_profile_read(ellsolve_t h, double *ms, int *launches, d
 
 uint64_t ellsolve_launch_count(ellsolve_t h) { return h ? h->launches : 0; }
 
+ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
+    ELLS_GUARD_BEGIN
+    if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
+    if (h->opts.precision != 1) throw Error(ELLSOLVE_ERR_ARG, "autotune needs precision 1");
+    cudaStream_t s = h->stream;
+    const LevelStore &L0 = h->lev[0];
+    const size_t nl = size_t(L0.ncol) * h->nz;
+    const bool rows = rows_eligible(*h, 0);
+    // one smoother sweep on level 0 of the handle's own buffers (zeroed)
+    check_cuda(cudaMemsetAsync(L0.u32[0].p, 0, nl * 4, s), "zero");
+    check_cuda(cudaMemsetAsync(L0.b32.p, 0, nl * 4, s), "zero");
+    std::vector<Lv<float>> hd{h->h32[0]};
+    std::vector<Item> items;
+    push_items(items, 0, L0.ncol, 0, 1, 0);
+    DevBuf dd, di;
+    upload(dd, hd, s);
+    upload(di, items, s);
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "event");
+    check_cuda(cudaEventCreate(&e1), "event");
+    const int candidates[] = {2, 3, 4, 5, 6};
+    int best = h->smooth_ctas_per_sm;
+    double best_ms = 1e300;
+    const int keep = h->smooth_ctas_per_sm;
+    for (int ctas : candidates) {
+        h->smooth_ctas_per_sm = ctas;
+        auto sweep = [&]() {
+            launch_smoother<float>(*h, s, dd.as<Lv<float>>(), di.as<Item>(), int(items.size()), 0.8,
+                                   h->nz, 0, rows);
+        };
+        sweep();  // warm-up
+        check_cuda(cudaEventRecord(e0, s), "record");
+        const int reps = 3;
+        for (int r = 0; r < reps; ++r) sweep();
+        check_cuda(cudaEventRecord(e1, s), "record");
+        check_cuda(cudaEventSynchronize(e1), "sync");
+        float ms = 0.f;
+        check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+        if (ms / reps < best_ms) {
+            best_ms = ms / reps;
+            best = ctas;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->smooth_ctas_per_sm = rows ? best : keep;
+    if (h->plan) h->plan->drop_graph();
+    if (out_ctas) *out_ctas = h->smooth_ctas_per_sm;
+    if (out_ms) *out_ms = best_ms;
+    return ELLSOLVE_OK;
+    ELLS_GUARD_END
+}
+
 }  // extern "C"

@@ -66,6 +66,7 @@ _SIGS = {
     "ellsolve_profile_enable": (_st, [_vp, _i]),
     "ellsolve_profile_read": (_st, [_vp, C.POINTER(_d), C.POINTER(_i), C.POINTER(_d)]),
     "ellsolve_launch_count": (C.c_uint64, [_vp]),
+    "ellsolve_autotune": (_st, [_vp, C.POINTER(_i), C.POINTER(_d)]),
     "ellsolve_server_create": (_st, [C.c_size_t, _i, _vp, C.POINTER(_vp)]),
     "ellsolve_submit": (_st, [_vp, C.POINTER(ellsolve_grid), _d, _d, C.POINTER(C.c_double), _vp,
                               _vp, _d, _i, C.POINTER(C.c_uint64)]),
@@ -194,6 +195,12 @@ class Solver:
 
     def launch_count(self):
         return int(_lib.ellsolve_launch_count(self.h))
+
+    def autotune(self):
+        """Pick the smoother's CTAs per SM by timing; returns (ctas, ms per sweep)."""
+        c, ms = C.c_int(), C.c_double()
+        check(_lib.ellsolve_autotune(self.h, C.byref(c), C.byref(ms)), "ellsolve_autotune")
+        return c.value, ms.value
 
 
 def solve_batch(solvers, rhs, xs, rtol=1e-8, maxit=50):

@@ -223,3 +223,19 @@ def test_batch_equals_alone(torch_mod, oracle_mod):
         assert ita == rb.iterations
         assert torch.equal(xa, xb)
         assert rb.rel_residual <= 1e-8
+
+
+def test_autotune_changes_no_result(torch_mod, oracle_mod):
+    """ellsolve_autotune only changes the smoother's occupancy cap: a solve
+    before and after tuning gives the same bits."""
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    sv = ellsolve.Solver(1, 32, 32, inputs.radial_levels(32, graded=True), 0.01, 1.0, precision=1)
+    f = torch.tensor(inputs.uniform_pm1(sv.shape(), member=9), device="cuda")
+    x1, x2 = torch.zeros_like(f), torch.zeros_like(f)
+    sv.solve(f, x1, rtol=1e-9, maxit=40)
+    ctas, ms = sv.autotune()
+    assert 2 <= ctas <= 6 and ms > 0
+    sv.solve(f, x2, rtol=1e-9, maxit=40)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
