@@ -250,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     achieved = (prof_bytes / (prof_ms * 1e-3) / 1e9) if prof_ms > 0 else None
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "smoother_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "smoother_traffic.txt")
     if os.path.exists(tfile):
         with open(tfile) as fh:
             tinfo = json.load(fh)
