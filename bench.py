@@ -155,6 +155,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_ranks(dist, ms, ms_e2e, cycles, e2e_cycles, device="cpu"):
+    """Whole-job figures over the ranks: the slowest rank's times, the summed
+    V-cycles (each rank solves its own problem of N unknowns)."""
+    import torch
+    t = torch.tensor([ms, ms_e2e, float(cycles), float(e2e_cycles)], dtype=torch.float64,
+                     device=device)
+    tmax, tsum = t.clone(), t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tmax[1]), float(tsum[2]), float(tsum[3])
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -231,15 +243,9 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms_e2e = h0.elapsed_time(h1)
 
-    t = torch.tensor([ms, ms_e2e, float(cycles), float(e2e_cycles)], dtype=torch.float64,
-                     device="cuda")
     if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms, ms_e2e = float(tmax[0]), float(tmax[1])
-        cycles, e2e_cycles = float(tsum[2]), float(tsum[3])
+        ms, ms_e2e, cycles, e2e_cycles = aggregate_ranks(dist, ms, ms_e2e, cycles, e2e_cycles,
+                                                         device="cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
