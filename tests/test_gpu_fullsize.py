@@ -1,0 +1,67 @@
+"""Parity at full size, in the launch configuration the benchmark times: the
+cubed sphere 6 x 512 x 512 x 128 (201 M unknowns, graded levels,
+omega^2 = 0.01, lambda = 1), the mixed-precision multigrid solve with the CUDA
+graph and the autotuned smoother, to relative residual 1e-5.
+
+The oracle cannot repeat the whole solve at this size in seconds, so it checks
+the result through properties that hold at any size:
+  * its own FP64 residual of the returned solution meets the tolerance and
+    agrees with the residual the library reports;
+  * the library's FP64 operator applied to that solution equals the oracle's,
+    in relative L2 and on a sample of single cells, within 16x the oracle's own
+    rounding sensitivity (A x cancels for a converged x);
+"""
+import numpy as np
+import pytest
+
+from paper_1307_2036_gb300 import inputs
+from gpu_util import rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+KIND, N, NZ, W2, L2, RTOL = 1, 512, 128, 0.01, 1.0, 1e-5
+
+
+def test_sphere512_solve_meets_tolerance_in_oracle_residual(oracle_mod):
+    torch = require_gpu()
+    from paper_1307_2036_gb300 import ellsolve
+    r = inputs.radial_levels(NZ, graded=True)
+    shape = (NZ, 6, N, N)
+    f = inputs.smooth_per_panel(inputs.gaussian(shape, member=0), sweeps=3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sv = ellsolve.Solver(KIND, N, NZ, r, W2, L2, precision=1, use_graph=1, inner_cycles=2,
+                             stream=stream.cuda_stream)
+        fd = torch.from_numpy(f).to("cuda")
+        x = torch.zeros_like(fd)
+    stream.synchronize()
+    sv.autotune()
+    st, res = sv.solve(fd, x, rtol=RTOL, maxit=60)
+    assert st == ellsolve.OK and res.rel_residual <= RTOL
+    with torch.cuda.stream(stream):
+        y = torch.empty_like(x)
+        sv.apply(x, y)
+    stream.synchronize()
+    xh = x.cpu().numpy()
+    yh = y.cpu().numpy()
+    del fd, x, y
+    sv.close()
+
+    og = oracle_mod.Grid(KIND, N, NZ, r, W2, L2)
+    b = og.volumes() * f
+    rr = og.residual(b, xh)
+    rel = np.linalg.norm(rr) / np.linalg.norm(b)
+    assert rel <= RTOL
+    assert abs(rel - res.rel_residual) <= 1e-3 * rel
+    ya = og.apply(xh)
+    # A x of a converged solution cancels (A x ~ b while the vertical terms are
+    # large), so two correct FP64 evaluations differ by ~eps |A| |x|: the bound
+    # is 16x the oracle's own change under 4-ulp perturbations of x
+    eps = np.finfo(np.float64).eps
+    rng = np.random.default_rng(5)
+    yp = og.apply(xh * (1.0 + 4 * eps * rng.uniform(-1.0, 1.0, xh.shape)))
+    assert rel_l2(yh, ya) <= max(1e-13, 16 * rel_l2(yp, ya))
+    idx = rng.integers(0, ya.size, 4096)
+    d_lib = np.abs(yh.reshape(-1)[idx] - ya.reshape(-1)[idx])
+    d_self = np.abs(yp.reshape(-1)[idx] - ya.reshape(-1)[idx])
+    assert np.max(d_lib) <= 16 * np.max(d_self) + 1e-13 * np.abs(ya).max()
