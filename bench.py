@@ -285,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
             "l2_policy": "inputs larger than L2 (FP32 hierarchy %.1f GB)" % (N * 16 / 3 * 4 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "k_smooth<float> finest level (line-Jacobi sweep)",
+                     "kernel": "k_smooth_tw finest level (FP32 line-Jacobi sweep, twisted elimination)",
                      "launches_timed": prof_n, "peak_source": peak_kind},
         "cpu_baseline": {"value": cpu_rate, "unit": "unknowns*V-cycles/s", "cores": 1,
                          "kind": "oracle", "sample": cpu_desc},
@@ -426,7 +426,7 @@ def run_serving(torch, stream, count, rate=200.0, budget=96 << 30, slots=16):
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
-KERNEL_REV = "smooth-v7-pairs-f32x2"
+KERNEL_REV = "smooth-v8-twisted"
 
 
 def main():

@@ -192,13 +192,20 @@ uint64_t ellsolve_launch_count(ellsolve_t h);
 
 /* ---- autotuning ----
  * Times the FP32 line smoother on the handle's finest level for each candidate
- * number of resident CTAs per SM (the occupancy cap bounds the L2 working set
- * of the back substitution) and keeps the fastest for later solves on this
- * handle and for batches led by it.  The choice changes no result (same
- * arithmetic, different scheduling).  Uses the handle's own FP32 buffers as
- * scratch: call it between solves.  precision 1 only.  out_ctas / out_ms
- * (nullable) receive the chosen cap and its time per sweep. */
+ * pair (resident CTAs per SM, depth of its shared-memory staging ring) and
+ * keeps the fastest for later solves on this handle and for batches led by it.
+ * The occupancy cap bounds the L2 working set of the back substitution; the
+ * ring depth trades prefetch distance against shared memory per CTA.  The
+ * choice changes no result (same arithmetic, different scheduling).  Uses the
+ * handle's own FP32 buffers as scratch: call it between solves.  precision 1
+ * only.  out_ctas / out_ms (nullable) receive the chosen cap and its time per
+ * sweep.  The paper has no counterpart (its kernels are tuned by hand). */
 ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms);
+/* Set or read the two tuning values directly: ctas_per_sm 0..16 (0 = as many
+ * as fit), ring 4 or 8 steps; ERR_ARG outside those.  No result depends on
+ * them. */
+ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring);
+ellsolve_status ellsolve_get_tuning(ellsolve_t h, int *ctas_per_sm, int *ring);
 
 /* ---- serving: continuous batching of independent solves ----
  * A server owns one CUDA stream's worth of work; submitted requests are admitted

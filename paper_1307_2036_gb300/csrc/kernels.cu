@@ -776,6 +776,336 @@ __global__ void __launch_bounds__(kT2) k_smooth_rows2(const Lv<float> *__restric
 }
 
 // ---------------------------------------------------------------------------
+// Line smoother with twisted elimination, one column per thread.  The
+// tridiagonal system of a column (Algorithm Thomas, excess form) is eliminated
+// from both ends at once: levels 0..m-1 upwards and levels nz-1..m downwards
+// (m = nz/2) as the two halves of packed FP32x2 arithmetic.  Step s handles
+// levels k = s and k' = nz-1-s.  The halves meet at the face between m-1 and
+// m, where the two remaining equations
+//     x_{m-1} = f'_{m-1} + c'_{m-1} x_m,   x_m = g'_m + d'_m x_{m-1}
+// give x_{m-1} = (f' + c' g') / (1 - c' d'), with 1 - c' d' formed without
+// cancellation as rho_b + c' rho_t (rho = eps / m, the excess ratios of the
+// two last pivots); the back substitution then runs outwards.  Against
+// one-sided elimination this halves the sequential sweep, so the parked f'
+// and the iterate the back substitution re-reads stay in L2 for half as long,
+// and a warp holds 32 columns instead of 64: the L2 working set per unit of
+// throughput drops fourfold, which lets more warps run without spilling it to
+// DRAM.  Data movement per warp and step: the own rows of both levels with one
+// halo column each side, their b and rows j-1, j+1 (68 aligned 16-byte
+// cp.async chunks) into an FR-step shared-memory ring.  Pivots are recomputed
+// in the back substitution from one checkpoint per FR-step block (the same
+// instructions, so the same values).
+// ---------------------------------------------------------------------------
+constexpr int kTT = 128;                      // threads per CTA (one column each)
+constexpr int kLvF = 136;                     // floats per warp and level: [own 40][b 32][j-1 32][j+1 32]
+constexpr int kSlotF = 2 * kLvF;              // floats per warp and ring slot (levels k, k')
+constexpr int kOwnT = 0, kBT = 40, kJmT = 72, kJpT = 104;
+
+// ALN (every level of the launch has n % 32 == 0): a warp's 32 columns lie in
+// one row of one panel, so the neighbours off the staged rows are the west
+// neighbour of lane 0, the east one of lane 31, and the whole row j-1 or j+1
+// at a panel edge.  Their values are copied straight into the ring positions
+// that the skipped chunks would have filled, and no separate buffer is needed.
+__host__ __device__ inline size_t tw_smem_bytes(int max_nz, int fr, bool aln) {
+    return size_t(fr) * (kTT / 32) * kSlotF * 4 +          // ring
+           (aln ? 0 : size_t(fr) * 4 * kTT * 4) +          // neighbours off the staged rows
+           size_t(max_nz / 2 / fr) * kTT * 8 +             // pivot checkpoints
+           size_t(max_nz / 2) * 16;                        // (V_k, V_k') and (g_{k+1}, g_k')
+}
+
+template <int ZERO, int FR, bool ALN>
+__global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__ L,
+                                                   const Item *__restrict__ items, float rho,
+                                                   int max_nz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>(smem_raw);
+    float *fbr = ring + FR * (kTT / 32) * kSlotF;
+    float2 *cpt = reinterpret_cast<float2 *>(fbr + (ALN ? 0 : FR * 4 * kTT));
+    float2 *VP = cpt + (max_nz / 2 / FR) * kTT;
+    float2 *GH = VP + max_nz / 2;
+    const Item it = items[blockIdx.x];
+    const Lv<float> &d = L[it.lv];
+    const int nc = d.ncol, nz = d.nz, n = d.n, m = nz / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = it.col0 + tid;
+    const int c0w = it.col0 + 32 * warp;
+    const bool active = c < nc;
+    constexpr bool zero = ZERO == 1;
+    for (int i = tid; i < m; i += kTT) {
+        VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
+        GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
+    }
+    __syncthreads();
+    const float *__restrict__ u = d.u[it.in];
+    float *__restrict__ un = d.u[it.out];
+    const float *__restrict__ b = d.b;
+    const size_t snc = size_t(nc);
+    const size_t top0 = size_t(nz - 1) * snc;  // offset of level nz-1
+
+    float A = 1.f, sv = 1.f;
+    float2 t0 = f2(0.f), t1 = f2(0.f), t2 = f2(0.f), t3 = f2(0.f);
+    int4 nbr = make_int4(0, 0, 0, 0);
+    if (active) {
+        const Column<float> k0 = load_column(d, c);
+        A = k0.A;
+        sv = k0.s;
+        t0 = f2(k0.t0);
+        t1 = f2(k0.t1);
+        t2 = f2(k0.t2);
+        t3 = f2(k0.t3);
+        nbr = k0.nb;
+    }
+    // Neighbours off the staged rows (panel edges, periodic wrap, rows that
+    // change inside the warp): at most one horizontal (hd 0 west, 1 east) and
+    // one vertical (vd 2 south, 3 north) per column when n >= 4.
+    int hd = -1, vd = -1, hc = 0, vc = 0;
+    if (active && !zero) {
+        if (nbr.x != c - 1) { hd = 0; hc = nbr.x; }
+        if (nbr.y != c + 1) { hd = 1; hc = nbr.y; }
+        if (nbr.z != c - n) { vd = 2; vc = nbr.z; }
+        if (nbr.w != c + n) { vd = 3; vc = nbr.w; }
+    }
+    const bool warp_fb = !zero && __any_sync(0xffffffffu, hd >= 0 || vd >= 0);
+    const bool fh = hd >= 0, fv = vd >= 0;
+    // ALN: the staged chunks that the off-row neighbours replace (warp-uniform)
+    const bool skip_w = ALN && __shfl_sync(0xffffffffu, hd == 0, 0);
+    const bool skip_e = ALN && __shfl_sync(0xffffffffu, hd == 1, 31);
+    const bool skip_s = ALN && __shfl_sync(0xffffffffu, vd == 2, 0);
+    const bool skip_n = ALN && __shfl_sync(0xffffffffu, vd == 3, 0);
+
+    // chunk q of a step's 68: 0..33 level k, 34..67 level k'; within a level
+    // 0..9 own row with halo, 10..17 b, 18..25 row j-1, 26..33 row j+1
+    auto chunk = [&](int q, const float *&src, int &dst, int &nbytes, long long &adv, bool &iss) {
+        const bool tp = q >= 34;
+        const int r = tp ? q - 34 : q;
+        const float *base;
+        int scol;
+        bool use, skip = false;
+        if (r < 10) {
+            base = u; scol = c0w - 4 + 4 * r; dst = kOwnT + 4 * r; use = !zero;
+            skip = (r == 0 && skip_w) || (r == 9 && skip_e);
+        } else if (r < 18) {
+            base = b; scol = c0w + 4 * (r - 10); dst = kBT + 4 * (r - 10); use = true;
+        } else if (r < 26) {
+            base = u; scol = c0w - n + 4 * (r - 18); dst = kJmT + 4 * (r - 18); use = !zero;
+            skip = skip_s;
+        } else {
+            base = u; scol = c0w + n + 4 * (r - 26); dst = kJpT + 4 * (r - 26); use = !zero;
+            skip = skip_n;
+        }
+        if (tp) dst += kLvF;
+        use = use && q < 68 && scol >= 0 && scol + 4 <= nc;
+        src = use ? base + (tp ? top0 : 0) + scol : b;
+        nbytes = use ? 16 : 0;
+        adv = use ? (tp ? -(long long)nc : (long long)nc) : 0;
+        iss = q < 68 && !skip;
+    };
+    const float *pa, *pb, *pc;
+    int da, db, dc, na, nb, ncb;
+    long long adva, advb, advc;
+    bool ia, ib, ic;
+    chunk(lane, pa, da, na, adva, ia);
+    chunk(lane + 32, pb, db, nb, advb, ib);
+    chunk(lane + 64, pc, dc, ncb, advc, ic);
+    const float *ph_b = u + hc, *pv_b = u + vc, *ph_t = u + top0 + hc, *pv_t = u + top0 + vc;
+    // ALN: ring positions of this lane's off-row neighbours
+    const int hdst = kOwnT + (hd == 0 ? 3 : 36);
+    const int vdst = (vd == 2 ? kJmT : kJpT) + lane;
+    float *wring = ring + warp * kSlotF;
+    float *sa = wring + da, *sb2 = wring + db, *sc = wring + dc;
+    float *fbt = fbr + tid;
+
+    auto issue = [&](int slot) {
+        const int so = slot * (kTT / 32) * kSlotF;
+        if (ia) cp_async16(sa + so, pa, na);
+        pa += adva;
+        if (ib) cp_async16(sb2 + so, pb, nb);
+        pb += advb;
+        if (ic) cp_async16(sc + so, pc, ncb);
+        pc += advc;
+        if (warp_fb) {
+            if (ALN) {
+                float *w = wring + so;
+                if (fh) {
+                    cp_async(w + hdst, ph_b, true);
+                    cp_async(w + kLvF + hdst, ph_t, true);
+                }
+                if (fv) {
+                    cp_async(w + vdst, pv_b, true);
+                    cp_async(w + kLvF + vdst, pv_t, true);
+                }
+            } else {
+                cp_async(fbt + (slot * 4 + 0) * kTT, ph_b, fh);
+                cp_async(fbt + (slot * 4 + 1) * kTT, pv_b, fv);
+                cp_async(fbt + (slot * 4 + 2) * kTT, ph_t, fh);
+                cp_async(fbt + (slot * 4 + 3) * kTT, pv_t, fv);
+            }
+            ph_b += snc;
+            pv_b += snc;
+            ph_t -= snc;
+            pv_t -= snc;
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll
+    for (int j = 0; j < FR - 1; ++j) issue(j);
+    const int own = kOwnT + 4 + lane;  // this thread's column in an own row
+    constexpr int kStride = (kTT / 32) * kSlotF;  // floats between ring slots
+    float2 u0 = f2(0.f), um = f2(0.f);
+    if (!zero) {
+        cp_async_wait<FR - 2>();
+        __syncwarp();
+        u0 = make_float2(wring[own], wring[kLvF + own]);
+    }
+    float2 ratio = f2(0.f), fp = f2(0.f), lo = f2(0.f), lo_g = f2(0.f);
+    Piv2 pv;
+    pv.cp = pv.inv = pv.ratio_next = f2(0.f);
+    float *fpb = un + c, *fpt = un + top0 + c;
+    const int nblk = m / FR;
+#pragma unroll 1
+    for (int kb = 0; kb < nblk; ++kb) {
+        const bool last = kb == nblk - 1;
+        if (active) cpt[kb * kTT + tid] = ratio;
+#pragma unroll
+        for (int j = 0; j < FR; ++j) {
+            const int s = kb * FR + j;
+            __syncwarp();
+            if (!last) {
+                issue((j + FR - 1) % FR);
+                cp_async_wait<FR - 2>();
+            } else {
+                if (j == 0) issue(FR - 1);
+                cp_async_wait_upto(FR - 2 - j);
+            }
+            __syncwarp();
+            const float *sk = wring + j * kStride;
+            float2 r = make_float2(sk[kBT + lane], sk[kLvF + kBT + lane]);
+            const float2 hi_g = GH[s], Vp = VP[s];
+            if (!zero) {
+                float2 up;
+                if (last && j == FR - 1) {
+                    // the meeting step: the next level of each half is the other half's
+                    up = make_float2(sk[kLvF + own], sk[own]);
+                } else {
+                    const float *sn = wring + ((j + 1) % FR) * kStride;
+                    up = make_float2(sn[own], sn[kLvF + own]);
+                }
+                float2 nw = make_float2(sk[own - 1], sk[kLvF + own - 1]);
+                float2 ne = make_float2(sk[own + 1], sk[kLvF + own + 1]);
+                float2 ns = make_float2(sk[kJmT + lane], sk[kLvF + kJmT + lane]);
+                float2 nn = make_float2(sk[kJpT + lane], sk[kLvF + kJpT + lane]);
+                if (!ALN && warp_fb) {
+                    const float2 vh = make_float2(fbt[(j * 4 + 0) * kTT], fbt[(j * 4 + 2) * kTT]);
+                    const float2 vv = make_float2(fbt[(j * 4 + 1) * kTT], fbt[(j * 4 + 3) * kTT]);
+                    nw = hd == 0 ? vh : nw;
+                    ne = hd == 1 ? vh : ne;
+                    ns = vd == 2 ? vv : ns;
+                    nn = vd == 3 ? vv : nn;
+                }
+                float2 horiz = __fmul2_rn(t0, sub2(u0, nw));
+                horiz = __ffma2_rn(t1, sub2(u0, ne), horiz);
+                horiz = __ffma2_rn(t2, sub2(u0, ns), horiz);
+                horiz = __ffma2_rn(t3, sub2(u0, nn), horiz);
+                float2 vert = __fmul2_rn(hi_g, sub2(u0, up));
+                vert = __ffma2_rn(lo_g, sub2(u0, um), vert);
+                float2 Au = __fmul2_rn(f2(A), __fmul2_rn(Vp, u0));
+                Au = __ffma2_rn(Vp, horiz, Au);
+                Au = __ffma2_rn(f2(A), vert, Au);
+                r = sub2(r, Au);
+                um = u0;
+                u0 = up;
+            }
+            const float2 hi = __fmul2_rn(f2(A), hi_g);
+            pv = pivot2(__fmul2_rn(Vp, f2(sv)), lo, hi, ratio);
+            fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
+            if (active) {
+                *fpb = fp.x;
+                *fpt = fp.y;
+            }
+            fpb += snc;
+            fpt -= snc;
+            ratio = pv.ratio_next;
+            lo = hi;
+            lo_g = hi_g;
+        }
+    }
+    // meeting of the halves: x_{m-1} and x_m from the two last equations
+    float2 x;
+    {
+        const float den = __fmaf_rn(pv.cp.x, pv.ratio_next.y, pv.ratio_next.x);
+        const float xb = __fmul_rn(__fmaf_rn(pv.cp.x, fp.y, fp.x), rcp(den));
+        x = make_float2(xb, __fmaf_rn(pv.cp.y, xb, fp.y));
+    }
+    __threadfence_block();  // the f' stores of this warp are seen by its copies below
+    __syncwarp();
+
+    // back substitution, step s = m-1 .. 0; slot fields [0..31] f'_k,
+    // [32..63] g'_k', [64..95] u_k, [96..127] u_k'
+    const int brow = lane >> 3;
+    const int bcol = c0w + 4 * (lane & 7);
+    const bool need = brow < 2 || !zero;
+    const int nbk = need && bcol + 4 <= nc ? 16 : 0;
+    const bool upw = brow & 1;  // the top half runs upwards from m
+    const float *pbk = nbk ? (brow < 2 ? (const float *)un : u) + size_t(upw ? m : m - 1) * snc + bcol
+                           : b;
+    const long long advk = nbk ? (upw ? (long long)nc : -(long long)nc) : 0;
+    float *sbk = wring + 32 * brow + 4 * (lane & 7);
+    auto issue_back = [&](int slot) {
+        cp_async16(sbk + slot * kStride, pbk, nbk);
+        pbk += advk;
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < FR - 1; ++j) issue_back(j);
+    float *uob = un + size_t(m - 1) * snc + c, *uot = un + size_t(m) * snc + c;
+#pragma unroll 1
+    for (int kb = nblk - 1; kb >= 0; --kb) {
+        float2 cpr[FR];
+        {
+            float2 rt = active ? cpt[kb * kTT + tid] : f2(0.f);
+            float2 l0 = kb == 0 ? f2(0.f) : __fmul2_rn(f2(A), GH[kb * FR - 1]);
+#pragma unroll
+            for (int j = 0; j < FR; ++j) {
+                const int s = kb * FR + j;
+                const float2 h1 = __fmul2_rn(f2(A), GH[s]);
+                const Piv2 q = pivot2(__fmul2_rn(VP[s], f2(sv)), l0, h1, rt);
+                cpr[j] = q.cp;
+                rt = q.ratio_next;
+                l0 = h1;
+            }
+        }
+        const bool last = kb == 0;
+#pragma unroll
+        for (int jj = FR - 1; jj >= 0; --jj) {
+            const int s = kb * FR + jj;
+            const int step = FR - 1 - jj;  // position within this block, from the middle out
+            __syncwarp();
+            if (!last) {
+                issue_back((step + FR - 1) % FR);
+                cp_async_wait<FR - 1>();
+            } else {
+                if (step == 0) issue_back(FR - 1);
+                cp_async_wait_upto(FR - 1 - step);
+            }
+            __syncwarp();
+            const float *sk = wring + step * kStride;
+            const float2 fk = make_float2(sk[lane], sk[32 + lane]);
+            const float2 uo = zero ? f2(0.f) : make_float2(sk[64 + lane], sk[96 + lane]);
+            if (s != m - 1) x = __ffma2_rn(cpr[jj], x, fk);
+            const float2 un2 = __ffma2_rn(f2(rho), x, uo);
+            if (active) {
+                __stcs(uob, un2.x);
+                __stcs(uot, un2.y);
+            }
+            uob -= snc;
+            uot += snc;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Residual / apply (Sec. 3.1 stencil).
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
@@ -976,7 +1306,8 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
 // ---------------------------------------------------------------------------
 // FP64 outer residual of the iterative refinement.
 // ---------------------------------------------------------------------------
-template <bool XZERO>
+// MODE 0: general x; 1: x = 0 (r = A V f); 2: x = 0, norm only (r32 untouched)
+template <int MODE>
 __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restrict__ L64,
                                                       const Lv<float> *__restrict__ L32,
                                                       const Item *__restrict__ items,
@@ -996,21 +1327,27 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         float *__restrict__ r32 = L32[it.lv].b;
         const float sc = float(scale[it.lv]);  // a power of two: exact in FP32
         const Column<double> col = load_column(d, c);
-        double um = 0.0, u0 = XZERO ? 0.0 : __ldg(x + c), up = 0.0, gk = __ldg(g);
         float colsum = 0.f;  // this column's sum of r^2 (only steers the stopping test)
-        // FP64 is the scarce unit here: the mass and horizontal terms are formed
-        // as V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding ~eps C_horiz
-        // relative to the mass term, far below the FP64 attainable residual);
-        // the large vertical couplings keep the difference form.
-        //   r = A (V_k f - vert) - V_k hm
+        if (MODE != 0) {
+            // memory-bound: unrolled so that many loads are in flight per thread
+#pragma unroll 8
+            for (int k = 0; k < nz; ++k) {
+                const size_t o = size_t(k) * nc;
+                const float rf = float(col.A * (__ldg(V + k) * __ldg(f + o + c)));
+                if (MODE == 1) r32[o + c] = rf * sc;
+                colsum = fmaf(rf, rf, colsum);
+            }
+        } else {
+            double um = 0.0, u0 = __ldg(x + c), up = 0.0, gk = __ldg(g);
+            // FP64 is the scarce unit here: the mass and horizontal terms are
+            // formed as V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding
+            // ~eps C_horiz relative to the mass term, far below the FP64
+            // attainable residual); the large vertical couplings keep the
+            // difference form.   r = A (V_k f - vert) - V_k hm
 #pragma unroll 2
-        for (int k = 0; k < nz; ++k) {
-            const size_t o = size_t(k) * nc;
-            const double Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
-            double r;
-            if (XZERO) {
-                r = col.A * (Vk * __ldg(f + o + c));
-            } else {
+            for (int k = 0; k < nz; ++k) {
+                const size_t o = size_t(k) * nc;
+                const double Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
                 up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
                 const double *row = x + o;
                 double hm = col.s * u0;
@@ -1019,14 +1356,14 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                 hm = fma(-col.t2, __ldg(row + col.nb.z), hm);
                 hm = fma(-col.t3, __ldg(row + col.nb.w), hm);
                 const double vert = fma(gk, u0 - um, gk1 * (u0 - up));
-                r = fma(-Vk, hm, col.A * fma(Vk, __ldg(f + o + c), -vert));
+                const double r = fma(-Vk, hm, col.A * fma(Vk, __ldg(f + o + c), -vert));
+                const float rf = float(r);
+                r32[o + c] = rf * sc;
+                colsum = fmaf(rf, rf, colsum);
+                um = u0;
+                u0 = up;
+                gk = gk1;
             }
-            const float rf = float(r);
-            r32[o + c] = rf * sc;
-            colsum = fmaf(rf, rf, colsum);
-            um = u0;
-            u0 = up;
-            gk = gk1;
         }
         acc = double(colsum);
     }
@@ -1048,6 +1385,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_update(const Lv<double> *__restrict
     double *__restrict__ x = d.u[0];
     const float *__restrict__ e = L32[it.lv].u[it.in];
     const double inv = 1.0 / scale[it.lv];
+#pragma unroll 8
     for (int k = 0; k < d.nz; ++k) {
         const size_t o = size_t(k) * nc + c;
         x[o] += double(__ldg(e + o)) * inv;
@@ -1305,6 +1643,46 @@ cudaError_t launch_smooth_rows2(cudaStream_t s, const Lv<float> *L, const Item *
     return launch_rows2_z<0>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
 
+template <int Z, int FR, bool ALN>
+static cudaError_t launch_tw_zfa(cudaStream_t s, const Lv<float> *L, const Item *items,
+                                 int nitems, float rho, int max_nz, int ctas_per_sm) {
+    size_t bytes = tw_smem_bytes(max_nz, FR, ALN);
+    if (ctas_per_sm > 0) {
+        const size_t cap = (size_t(228) * 1024) / size_t(ctas_per_sm) - 1024;
+        if (cap > bytes) bytes = cap;
+    }
+    cudaError_t e = set_smem(k_smooth_tw<Z, FR, ALN>, bytes);
+    if (e != cudaSuccess) return e;
+    k_smooth_tw<Z, FR, ALN><<<nitems, kTT, bytes, s>>>(L, items, rho, max_nz);
+    return cudaGetLastError();
+}
+
+template <int Z, int FR>
+static cudaError_t launch_tw_zf(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                                float rho, int max_nz, int ctas_per_sm, bool aligned) {
+    if (aligned) return launch_tw_zfa<Z, FR, true>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
+    return launch_tw_zfa<Z, FR, false>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
+}
+
+cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                             float rho, int max_nz, int zero_mode, int ctas_per_sm, int ring,
+                             bool aligned) {
+    if (nitems <= 0) return cudaSuccess;
+    if (ring == 8) {
+        if (zero_mode == 1)
+            return launch_tw_zf<1, 8>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
+        return launch_tw_zf<0, 8>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
+    }
+    if (zero_mode == 1)
+        return launch_tw_zf<1, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
+    return launch_tw_zf<0, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
+}
+
+bool smooth_tw_fits(int max_nz, int ring) {
+    return max_nz % 2 == 0 && (max_nz / 2) % ring == 0 &&
+           tw_smem_bytes(max_nz, ring, false) <= kSmemCap;
+}
+
 cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                                float rho, int max_nz, int zero_mode, int ctas_per_sm) {
     if (nitems <= 0) return cudaSuccess;
@@ -1353,8 +1731,9 @@ cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<f
                                const Item *items, int nitems, const double *scale,
                                double *partials, int x_is_zero) {
     if (nitems <= 0) return cudaSuccess;
-    if (x_is_zero) k_ir_residual<true><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
-    else k_ir_residual<false><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
+    if (x_is_zero == 2) k_ir_residual<2><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
+    else if (x_is_zero) k_ir_residual<1><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
+    else k_ir_residual<0><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,10 @@ cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *i
                                float rho, int max_nz, int zero_mode, int ctas_per_sm);
 // Same sweep with two columns per thread and packed FP32x2 arithmetic (64-thread CTAs
 // over the same 128-column items).
+cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                             float rho, int max_nz, int zero_mode, int ctas_per_sm, int ring,
+                             bool aligned);
+bool smooth_tw_fits(int max_nz, int ring);
 cudaError_t launch_smooth_rows2(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                                 float rho, int max_nz, int zero_mode, int ctas_per_sm);
 
@@ -51,7 +55,8 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 // Iterative-refinement outer step, per member m (items' lv = member index):
 //   r = A_P V_k f - A x   in FP64, f = L64[m].b (pointwise), x = L64[m].u[0],
 //   L32[m].b = float(r * scale[m]), partials[item] = sum of r^2.
-// x_is_zero: x = 0, so r = A_P V_k f without the stencil (start of a solve).
+// x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve);
+// 2 the same but only the norm (r32 is not written).
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
                                double *partials, int x_is_zero);

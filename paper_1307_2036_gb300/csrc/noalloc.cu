@@ -98,7 +98,8 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
     const Item *it = reinterpret_cast<const Item *>(base + off_items);
     const bool rows = sizeof(T) == 4 && rows_eligible(p, level);
     for (int sw = 0; sw < nsweeps; ++sw)
-        launch_smoother<T>(p, s, L, it + size_t(sw & 1) * per, per, rho, p.nz, 0, rows);
+        launch_smoother<T>(p, s, L, it + size_t(sw & 1) * per, per, rho, p.nz, 0, rows,
+                           p.lev[level].n % 32 == 0);
     if (nsweeps & 1)
         check_cuda(cudaMemcpyAsync(u, d.u[1], nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                    "copy back");

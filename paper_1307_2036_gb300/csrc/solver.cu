@@ -414,8 +414,10 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
         op.max_nz = 0;
         int nz_items = 0, z_items = 0;
         op.rows_ok = true;
+        op.aligned = true;
         for (auto [m, l] : ml) {
             if (!rows_level(m, l)) op.rows_ok = false;
+            if (mem[m]->lev[l].n % 32 != 0) op.aligned = false;
             MemberState &s = st[m];
             (s.zero[l] ? z_items : nz_items) += 1;
             push_items(items, base[m] + l, mem[m]->lev[l].ncol, s.cur[l], 1 - s.cur[l], s.zero[l]);
@@ -523,15 +525,21 @@ void Plan::sync_items() {
 // ---------------------------------------------------------------------------
 bool rows_eligible(const Problem &p, int level) {
     const LevelStore &Ls = p.lev[level];
-    return Ls.n % 4 == 0 && Ls.ncol % 4 == 0 && p.nz % 8 == 0 && smooth_rows_fits(p.nz);
+    if (Ls.n % 4 != 0 || Ls.ncol % 4 != 0) return false;
+    if (p.smooth_variant == 3) return p.nz % 16 == 0 && smooth_tw_fits(p.nz, 8);
+    return p.nz % 8 == 0 && smooth_rows_fits(p.nz);
 }
 
 template <typename T>
 void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
-                     double rho, int max_nz, int zero_mode, bool rows_ok) {
+                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned) {
     if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
         const Lv<float> *Lf = reinterpret_cast<const Lv<float> *>(L);
-        if (p.smooth_variant == 2)
+        if (p.smooth_variant == 3)
+            check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode,
+                                        p.smooth_ctas_per_sm, p.smooth_ring, aligned),
+                       "smooth_tw");
+        else if (p.smooth_variant == 2)
             check_cuda(launch_smooth_rows2(s, Lf, it, n, float(rho), max_nz, zero_mode,
                                            p.smooth_ctas_per_sm),
                        "smooth_rows2");
@@ -544,9 +552,9 @@ void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Ite
     }
 }
 template void launch_smoother<float>(const Problem &, cudaStream_t, const Lv<float> *,
-                                     const Item *, int, double, int, int, bool);
+                                     const Item *, int, double, int, int, bool, bool);
 template void launch_smoother<double>(const Problem &, cudaStream_t, const Lv<double> *,
-                                      const Item *, int, double, int, int, bool);
+                                      const Item *, int, double, int, int, bool, bool);
 static void count(Plan &pl, int n = 1) {
     for (Problem *p : pl.mem) p->launches += uint64_t(n);
 }
@@ -571,7 +579,7 @@ static void run_program(Plan &pl, const Program &prog) {
                 const bool timed = p0.prof && op.finest;
                 if (timed) p0.prof_mark_begin(s);
                 launch_smoother<T>(p0, s, L, it + op.off, op.n, op.rho, op.max_nz, op.zero_mode,
-                                   op.rows_ok);
+                                   op.rows_ok, op.aligned);
                 if (timed) p0.prof_mark_end(s, op.bytes);
                 count(pl);
                 break;
@@ -826,7 +834,7 @@ void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep
         r.hist.assign(1, 1.0);
     }
     ir_push_state(pl, run);
-    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
+    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 2);  // the norm only: it fixes the scale
     read_norms(pl, int(pl.mem.size()));
     for (int m = m0; m < m1; ++m) {
         MemberRun &r = *run[m];
@@ -1126,7 +1134,8 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
         case 2: {
             const bool rows = sizeof(T) == 4 && rows_eligible(p, level);
             for (int sw = 0; sw < nsweeps; ++sw)
-                launch_smoother<T>(p, s, L, it + sw * per, per, rho, p.nz, 0, rows);
+                launch_smoother<T>(p, s, L, it + sw * per, per, rho, p.nz, 0, rows,
+                                   p.lev[level].n % 32 == 0);
             if (nsweeps & 1)
                 check_cuda(cudaMemcpyAsync(out, tmp.p, nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                            "copy back");
@@ -1411,15 +1420,21 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
     cudaEvent_t e0, e1;
     check_cuda(cudaEventCreate(&e0), "event");
     check_cuda(cudaEventCreate(&e1), "event");
-    const int candidates[] = {2, 3, 4, 5, 6};
-    int best = h->smooth_ctas_per_sm;
+    // (resident CTAs per SM, ring depth) candidates of the smoother in use
+    std::vector<std::pair<int, int>> candidates;
+    if (h->smooth_variant == 3)
+        candidates = {{3, 8}, {4, 8}, {5, 8}, {3, 4}, {4, 4}, {5, 4}};
+    else
+        candidates = {{2, 8}, {3, 8}, {4, 8}, {5, 8}, {6, 8}};
+    int best = h->smooth_ctas_per_sm, best_ring = h->smooth_ring;
     double best_ms = 1e300;
-    const int keep = h->smooth_ctas_per_sm;
-    for (int ctas : candidates) {
+    const int keep = h->smooth_ctas_per_sm, keep_ring = h->smooth_ring;
+    for (auto [ctas, ring] : candidates) {
         h->smooth_ctas_per_sm = ctas;
+        h->smooth_ring = ring;
         auto sweep = [&]() {
             launch_smoother<float>(*h, s, dd.as<Lv<float>>(), di.as<Item>(), int(items.size()), 0.8,
-                                   h->nz, 0, rows);
+                                   h->nz, 0, rows, L0.n % 32 == 0);
         };
         sweep();  // warm-up
         check_cuda(cudaEventRecord(e0, s), "record");
@@ -1432,16 +1447,39 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
         if (ms / reps < best_ms) {
             best_ms = ms / reps;
             best = ctas;
+            best_ring = ring;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->smooth_ctas_per_sm = rows ? best : keep;
+    h->smooth_ring = rows ? best_ring : keep_ring;
     if (h->plan) h->plan->drop_graph();
     if (out_ctas) *out_ctas = h->smooth_ctas_per_sm;
     if (out_ms) *out_ms = best_ms;
     return ELLSOLVE_OK;
     ELLS_GUARD_END
 }
+ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring) {
+    ELLS_GUARD_BEGIN
+    if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
+    if (ctas_per_sm < 0 || ctas_per_sm > 16) throw Error(ELLSOLVE_ERR_ARG, "ctas_per_sm must be 0..16");
+    if (ring != 4 && ring != 8) throw Error(ELLSOLVE_ERR_ARG, "ring must be 4 or 8");
+    h->smooth_ctas_per_sm = ctas_per_sm;
+    h->smooth_ring = ring;
+    if (h->plan) h->plan->drop_graph();
+    return ELLSOLVE_OK;
+    ELLS_GUARD_END
+}
+
+ellsolve_status ellsolve_get_tuning(ellsolve_t h, int *ctas_per_sm, int *ring) {
+    ELLS_GUARD_BEGIN
+    if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
+    if (ctas_per_sm) *ctas_per_sm = h->smooth_ctas_per_sm;
+    if (ring) *ring = h->smooth_ring;
+    return ELLSOLVE_OK;
+    ELLS_GUARD_END
+}
+
 
 }  // extern "C"

@@ -89,6 +89,7 @@ struct Op {
     double bytes = 0.0;       // algorithmic bytes of the finest-level work
     int zero_mode = 0;        // smoother items: 0 none / 1 all start from zero, 2 mixed
     bool rows_ok = false;     // every level in the op suits the row-staged FP32 smoother
+    bool aligned = false;     // every level in the op has n % 32 == 0
     int member = 0, level = 0, buf = 0;  // kMemset target
 };
 
@@ -156,8 +157,10 @@ struct Problem {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_graph;
     int ev_next = 0, ev_graph_used = 0;
-    int smooth_ctas_per_sm = 4;  // row-staged smoother occupancy cap (0: as many as fit)
-    int smooth_variant = 2;      // FP32 row-staged smoother: 2 two columns/thread, 1 one
+    int smooth_ctas_per_sm = 3;  // row-staged smoother occupancy cap (0: as many as fit)
+    int smooth_ring = 8;         // twisted smoother's staging ring depth (4 or 8 steps)
+    int smooth_variant = 3;      // FP32 row-staged smoother: 3 twisted (one column/thread),
+                                 // 2 two columns/thread, 1 one column/thread
     double prof_ms = 0.0, prof_bytes = 0.0;
     long prof_count = 0;
     std::vector<double> ev_free_bytes, ev_graph_bytes;  // bytes per recorded pair
@@ -196,7 +199,7 @@ ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res
 // the generic kernel.
 template <typename T>
 void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
-                     double rho, int max_nz, int zero_mode, bool rows_ok);
+                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned);
 bool rows_eligible(const Problem &p, int level);
 
 ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,

@@ -67,6 +67,8 @@ _SIGS = {
     "ellsolve_profile_read": (_st, [_vp, C.POINTER(_d), C.POINTER(_i), C.POINTER(_d)]),
     "ellsolve_launch_count": (C.c_uint64, [_vp]),
     "ellsolve_autotune": (_st, [_vp, C.POINTER(_i), C.POINTER(_d)]),
+    "ellsolve_set_tuning": (_st, [_vp, _i, _i]),
+    "ellsolve_get_tuning": (_st, [_vp, C.POINTER(_i), C.POINTER(_i)]),
     "ellsolve_server_create": (_st, [C.c_size_t, _i, _vp, C.POINTER(_vp)]),
     "ellsolve_submit": (_st, [_vp, C.POINTER(ellsolve_grid), _d, _d, C.POINTER(C.c_double), _vp,
                               _vp, _d, _i, C.POINTER(C.c_uint64)]),
@@ -201,6 +203,15 @@ class Solver:
         c, ms = C.c_int(), C.c_double()
         check(_lib.ellsolve_autotune(self.h, C.byref(c), C.byref(ms)), "ellsolve_autotune")
         return c.value, ms.value
+
+    def set_tuning(self, ctas_per_sm, ring):
+        check(_lib.ellsolve_set_tuning(self.h, int(ctas_per_sm), int(ring)), "set_tuning")
+
+    def tuning(self):
+        """(resident CTAs per SM, ring depth) of the FP32 line smoother."""
+        c, r = C.c_int(), C.c_int()
+        check(_lib.ellsolve_get_tuning(self.h, C.byref(c), C.byref(r)), "get_tuning")
+        return c.value, r.value
 
 
 def solve_batch(solvers, rhs, xs, rtol=1e-8, maxit=50):

@@ -206,7 +206,10 @@ def test_batch_equals_alone(torch_mod, oracle_mod):
     """Members of a batch give bit-identical results to the same solves alone."""
     from paper_1307_2036_gb300 import ellsolve
     torch = torch_mod
-    specs = [(1, 8, 16, 0.01, 1.0), (0, 24, 12, 0.05, 4.0), (1, 12, 8, 0.002, 0.5)]
+    # a 32-column-aligned finest level (n = 32) next to unaligned ones, so a
+    # batched launch mixes levels the aligned smoother variant would take alone
+    specs = [(1, 8, 16, 0.01, 1.0), (0, 24, 12, 0.05, 4.0), (1, 12, 8, 0.002, 0.5),
+             (1, 32, 32, 0.01, 1.0), (0, 64, 16, 0.02, 2.0)]
     solvers, rhs = [], []
     for m, (kind, n, nz, w2, l2) in enumerate(specs):
         s = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=True), w2, l2, precision=1)
