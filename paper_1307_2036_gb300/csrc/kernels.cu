@@ -898,7 +898,10 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
         src = use ? base + (tp ? top0 : 0) + scol : b;
         nbytes = use ? 16 : 0;
         adv = use ? (tp ? -(long long)nc : (long long)nc) : 0;
-        iss = q < 68 && !skip;
+        // Chunks without data are not issued at all: what they would fill is
+        // either unused (zero sweep, inactive columns) or replaced by the
+        // off-row neighbours before use.
+        iss = use && !skip;
     };
     const float *pa, *pb, *pc;
     int da, db, dc, na, nb, ncb;
@@ -1052,7 +1055,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     const long long advk = nbk ? (upw ? (long long)nc : -(long long)nc) : 0;
     float *sbk = wring + 32 * brow + 4 * (lane & 7);
     auto issue_back = [&](int slot) {
-        cp_async16(sbk + slot * kStride, pbk, nbk);
+        if (nbk) cp_async16(sbk + slot * kStride, pbk, nbk);
         pbk += advk;
         cp_async_commit();
     };
