@@ -223,6 +223,16 @@ ellsolve_status ellsolve_poll(ellsolve_server_t s, uint64_t ticket, int timeout_
                               ellsolve_result *res);
 void ellsolve_server_destroy(ellsolve_server_t s);
 
+/* ---- self-test ----
+ * Runs the library's device self-checks on the current device: the exact
+ * binary32 <-> binary64 conversions the FP64 refinement kernels do with integer
+ * arithmetic are compared bit for bit with the hardware conversions over
+ * `samples` pseudo-random bit patterns (a quarter of them on rounding ties).
+ * *mismatches (nullable) receives the count.  Returns OK when it is zero,
+ * ERR_CUDA with a message otherwise.  Allocates 8 bytes of device memory.
+ * The paper has no counterpart. */
+ellsolve_status ellsolve_selftest(uint64_t samples, uint64_t *mismatches);
+
 const char *ellsolve_last_error(void);
 
 #ifdef __cplusplus

@@ -30,6 +30,43 @@ __device__ __forceinline__ float rcp(float x) {
 }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
+// Exact conversions between binary32 and binary64 by integer arithmetic.  The
+// FP64 pipe of this GPU is narrow and the hardware conversions between the
+// two formats issue on it; these issue on the integer units instead.  Cases
+// outside the common one (zero, subnormal, Inf, NaN, exponent out of range)
+// take the hardware path, which gives the same result.  Both are checked
+// against the hardware conversions by ellsolve_selftest.
+//
+// binary64 -> binary32, round to nearest, ties to even: the 52-bit
+// significand rounded to 23 bits, the exponent rebiased (1023 - 127 = 896).
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const int e = static_cast<int>((hi >> 20) & 0x7ffu) - 896;
+    if (e < 1 || e > 254) return __double2float_rn(d);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the kept 23 bits
+    const unsigned rest = lo & 0x1fffffffu;                   // the 29 bits rounded away
+    unsigned f = (hi & 0x80000000u) | (static_cast<unsigned>(e) << 23) | m;
+    // a carry out of the significand raises the exponent (to Inf past 254)
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+
+// v * 2^k in binary64, exact: the fields of v moved into binary64 position.
+__device__ __forceinline__ double f32_to_f64_pow2(float v, int k) {
+    const unsigned u = __float_as_uint(v);
+    const int e = static_cast<int>((u >> 23) & 0xffu);
+    const int E = e + 896 + k;
+    if (e == 0 || e == 255 || E < 1 || E > 2046) {
+        const double p = __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+        return static_cast<double>(v) * p;  // |k| <= 1022 here
+    }
+    const unsigned long long bits = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
+                                    (static_cast<unsigned long long>(E) << 52) |
+                                    (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1332,40 +1369,47 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         const Column<double> col = load_column(d, c);
         float colsum = 0.f;  // this column's sum of r^2 (only steers the stopping test)
         if (MODE != 0) {
-            // memory-bound: unrolled so that many loads are in flight per thread
+            // x = 0: r = b = A_P V_k f, needed only in FP32 (the inner
+            // right-hand side and its norm), formed in FP32 from the FP32
+            // copies of A_P and V_k
+            const Lv<float> &e32 = L32[it.lv];
+            const float A32 = e32.area[c];
 #pragma unroll 8
             for (int k = 0; k < nz; ++k) {
                 const size_t o = size_t(k) * nc;
-                const float rf = float(col.A * (__ldg(V + k) * __ldg(f + o + c)));
+                const float rf =
+                    __fmul_rn(__fmul_rn(A32, __ldg(e32.V + k)), f64_to_f32_rn(__ldg(f + o + c)));
                 if (MODE == 1) r32[o + c] = rf * sc;
                 colsum = fmaf(rf, rf, colsum);
             }
         } else {
-            double um = 0.0, u0 = __ldg(x + c), up = 0.0, gk = __ldg(g);
-            // FP64 is the scarce unit here: the mass and horizontal terms are
-            // formed as V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding
-            // ~eps C_horiz relative to the mass term, far below the FP64
-            // attainable residual); the large vertical couplings keep the
-            // difference form.   r = A (V_k f - vert) - V_k hm
+            // FP64 is the scarce unit here (about 11 FP64 instructions per
+            // unknown).  The mass and horizontal terms are formed as
+            // V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding ~eps C_horiz
+            // relative to the mass term, far below the FP64 attainable
+            // residual); the vertical term as the difference of the face fluxes
+            // G_{k+1} (u_k - u_{k+1}), carried from one level to the next
+            // (G_0 = G_nz = 0).   r = A (V_k f - vert) - V_k hm
+            double u0 = __ldg(x + c), flux_lo = 0.0;
 #pragma unroll 2
             for (int k = 0; k < nz; ++k) {
                 const size_t o = size_t(k) * nc;
                 const double Vk = __ldg(V + k), gk1 = __ldg(g + k + 1);
-                up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
+                const double up = (k + 1 < nz) ? __ldg(x + o + nc + c) : 0.0;
                 const double *row = x + o;
                 double hm = col.s * u0;
                 hm = fma(-col.t0, __ldg(row + col.nb.x), hm);
                 hm = fma(-col.t1, __ldg(row + col.nb.y), hm);
                 hm = fma(-col.t2, __ldg(row + col.nb.z), hm);
                 hm = fma(-col.t3, __ldg(row + col.nb.w), hm);
-                const double vert = fma(gk, u0 - um, gk1 * (u0 - up));
+                const double flux_hi = gk1 * (u0 - up);
+                const double vert = flux_hi - flux_lo;
                 const double r = fma(-Vk, hm, col.A * fma(Vk, __ldg(f + o + c), -vert));
-                const float rf = float(r);
+                const float rf = f64_to_f32_rn(r);
                 r32[o + c] = rf * sc;
                 colsum = fmaf(rf, rf, colsum);
-                um = u0;
+                flux_lo = flux_hi;
                 u0 = up;
-                gk = gk1;
             }
         }
         acc = double(colsum);
@@ -1387,11 +1431,22 @@ __global__ void __launch_bounds__(kBlk) k_ir_update(const Lv<double> *__restrict
     if (c >= nc) return;
     double *__restrict__ x = d.u[0];
     const float *__restrict__ e = L32[it.lv].u[it.in];
-    const double inv = 1.0 / scale[it.lv];
+    // x += e / scale with scale = 2^-k: the conversion and the scaling are one
+    // exact change of exponent, and the add is the only FP64 instruction
+    const long long sb = __double_as_longlong(scale[it.lv]);
+    const int k = 1023 - static_cast<int>((sb >> 52) & 0x7ff);
+    if ((sb & ((1ll << 52) - 1)) == 0 && sb > 0) {
 #pragma unroll 8
-    for (int k = 0; k < d.nz; ++k) {
-        const size_t o = size_t(k) * nc + c;
-        x[o] += double(__ldg(e + o)) * inv;
+        for (int l = 0; l < d.nz; ++l) {
+            const size_t o = size_t(l) * nc + c;
+            x[o] += f32_to_f64_pow2(__ldg(e + o), k);
+        }
+    } else {
+        const double inv = 1.0 / scale[it.lv];
+        for (int l = 0; l < d.nz; ++l) {
+            const size_t o = size_t(l) * nc + c;
+            x[o] += double(__ldg(e + o)) * inv;
+        }
     }
 }
 
@@ -1727,6 +1782,43 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
                                int mode) {
     if (nitems <= 0) return cudaSuccess;
     k_prolong_add<T><<<nitems, kBlk, 0, s>>>(L, items, mode);
+    return cudaGetLastError();
+}
+
+// Self-test of the integer-arithmetic conversions against the hardware ones
+// over n bit patterns from a counter hash (SplitMix64 finaliser), with every
+// fourth binary64 sample moved onto a rounding tie; mismatches are counted.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_selftest_conv(unsigned long long n, unsigned long long *bad) {
+    unsigned long long local = 0;
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n;
+         i += 256ull * gridDim.x) {
+        unsigned long long h = mix64(i);
+        if ((i & 3) == 0) h = (h & ~0x1fffffffull) | 0x10000000ull;  // exact tie
+        const double d = __longlong_as_double(static_cast<long long>(h));
+        const float a = f64_to_f32_rn(d), r = __double2float_rn(d);
+        const bool same = __float_as_uint(a) == __float_as_uint(r) || (isnan(a) && isnan(r));
+        local += same ? 0 : 1;
+        const unsigned long long g = mix64(h);
+        const float v = __uint_as_float(static_cast<unsigned>(g));
+        const int k = static_cast<int>((g >> 32) % 129ull) - 64;
+        const double p = __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+        const double x = f32_to_f64_pow2(v, k), y = static_cast<double>(v) * p;
+        const bool same2 = __double_as_longlong(x) == __double_as_longlong(y) ||
+                           (isnan(x) && isnan(y));
+        local += same2 ? 0 : 1;
+    }
+    if (local) atomicAdd(bad, local);
+}
+
+cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned long long *bad) {
+    k_selftest_conv<<<1024, 256, 0, s>>>(n, bad);
     return cudaGetLastError();
 }
 

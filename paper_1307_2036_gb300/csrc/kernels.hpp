@@ -57,6 +57,7 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 //   L32[m].b = float(r * scale[m]), partials[item] = sum of r^2.
 // x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve);
 // 2 the same but only the norm (r32 is not written).
+cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned long long *bad);
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
                                double *partials, int x_is_zero);

@@ -1460,6 +1460,22 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
     return ELLSOLVE_OK;
     ELLS_GUARD_END
 }
+ellsolve_status ellsolve_selftest(uint64_t samples, uint64_t *mismatches) {
+    ELLS_GUARD_BEGIN
+    DevBuf bad;
+    bad.alloc(sizeof(unsigned long long));
+    check_cuda(cudaMemset(bad.p, 0, sizeof(unsigned long long)), "memset");
+    check_cuda(launch_selftest_conv(0, samples, static_cast<unsigned long long *>(bad.p)),
+               "selftest");
+    unsigned long long h = 0;
+    check_cuda(cudaMemcpy(&h, bad.p, sizeof(h), cudaMemcpyDeviceToHost), "selftest copy");
+    if (mismatches) *mismatches = h;
+    if (h != 0) throw Error(ELLSOLVE_ERR_CUDA, "conversion self-test: " + std::to_string(h) +
+                                                   " mismatches");
+    return ELLSOLVE_OK;
+    ELLS_GUARD_END
+}
+
 ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring) {
     ELLS_GUARD_BEGIN
     if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");

@@ -68,6 +68,7 @@ _SIGS = {
     "ellsolve_launch_count": (C.c_uint64, [_vp]),
     "ellsolve_autotune": (_st, [_vp, C.POINTER(_i), C.POINTER(_d)]),
     "ellsolve_set_tuning": (_st, [_vp, _i, _i]),
+    "ellsolve_selftest": (_st, [C.c_uint64, C.POINTER(C.c_uint64)]),
     "ellsolve_get_tuning": (_st, [_vp, C.POINTER(_i), C.POINTER(_i)]),
     "ellsolve_server_create": (_st, [C.c_size_t, _i, _vp, C.POINTER(_vp)]),
     "ellsolve_submit": (_st, [_vp, C.POINTER(ellsolve_grid), _d, _d, C.POINTER(C.c_double), _vp,
@@ -212,6 +213,14 @@ class Solver:
         c, r = C.c_int(), C.c_int()
         check(_lib.ellsolve_get_tuning(self.h, C.byref(c), C.byref(r)), "get_tuning")
         return c.value, r.value
+
+
+def selftest(samples=1 << 24):
+    """Device self-check of the library's integer-arithmetic conversions;
+    returns the number of mismatches (raises if there are any)."""
+    bad = C.c_uint64()
+    check(_lib.ellsolve_selftest(int(samples), C.byref(bad)), "ellsolve_selftest")
+    return bad.value
 
 
 def solve_batch(solvers, rhs, xs, rtol=1e-8, maxit=50):
