@@ -441,7 +441,7 @@ def main():
                     help="skip the ensemble and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests in the bounded serving sample")
-    ap.add_argument("--inner-cycles", type=int, default=2,
+    ap.add_argument("--inner-cycles", type=int, default=3,
                     help="FP32 V-cycles per FP64 refinement step")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -78,7 +78,7 @@ typedef struct {
     int coarsest_min; /* coarsen while n is even and n/2 >= coarsest_min (4) */
     int max_levels;   /* cap on the number of levels, <= 0: no cap */
     int prolong;      /* 0: bilinear (cell-centred), 1: piecewise constant */
-    int inner_cycles; /* precision 1: FP32 V-cycles per FP64 refinement step (2) */
+    int inner_cycles; /* precision 1: FP32 V-cycles per FP64 refinement step (3) */
     int use_graph;    /* 1: replay the per-iteration work as a CUDA graph */
 } ellsolve_opts;
 

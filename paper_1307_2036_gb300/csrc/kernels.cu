@@ -39,11 +39,19 @@ __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 //
 // binary64 -> binary32, round to nearest, ties to even: the 52-bit
 // significand rounded to 23 bits, the exponent rebiased (1023 - 127 = 896).
+// The rare cases go through functions that are not inlined, so that the
+// compiler cannot turn the branch into predicated FP64 work on every element.
+__device__ __noinline__ float f64_to_f32_slow(double d) { return __double2float_rn(d); }
+__device__ __noinline__ double f32_to_f64_pow2_slow(float v, int k) {
+    const double p = __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+    return static_cast<double>(v) * p;  // |k| <= 1022 here
+}
+
 __device__ __forceinline__ float f64_to_f32_rn(double d) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
     const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
     const int e = static_cast<int>((hi >> 20) & 0x7ffu) - 896;
-    if (e < 1 || e > 254) return __double2float_rn(d);
+    if (e < 1 || e > 254) return f64_to_f32_slow(d);
     const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the kept 23 bits
     const unsigned rest = lo & 0x1fffffffu;                   // the 29 bits rounded away
     unsigned f = (hi & 0x80000000u) | (static_cast<unsigned>(e) << 23) | m;
@@ -57,10 +65,7 @@ __device__ __forceinline__ double f32_to_f64_pow2(float v, int k) {
     const unsigned u = __float_as_uint(v);
     const int e = static_cast<int>((u >> 23) & 0xffu);
     const int E = e + 896 + k;
-    if (e == 0 || e == 255 || E < 1 || E > 2046) {
-        const double p = __longlong_as_double(static_cast<long long>(k + 1023) << 52);
-        return static_cast<double>(v) * p;  // |k| <= 1022 here
-    }
+    if (e == 0 || e == 255 || E < 1 || E > 2046) return f32_to_f64_pow2_slow(v, k);
     const unsigned long long bits = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
                                     (static_cast<unsigned long long>(E) << 52) |
                                     (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
@@ -1374,13 +1379,21 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
             // copies of A_P and V_k
             const Lv<float> &e32 = L32[it.lv];
             const float A32 = e32.area[c];
-#pragma unroll 8
-            for (int k = 0; k < nz; ++k) {
-                const size_t o = size_t(k) * nc;
-                const float rf =
-                    __fmul_rn(__fmul_rn(A32, __ldg(e32.V + k)), f64_to_f32_rn(__ldg(f + o + c)));
-                if (MODE == 1) r32[o + c] = rf * sc;
-                colsum = fmaf(rf, rf, colsum);
+            constexpr int B = 8;  // eight levels' loads are issued before their conversions
+            for (int k0 = 0; k0 < nz; k0 += B) {
+                double fv[B];
+#pragma unroll
+                for (int j = 0; j < B; ++j) fv[j] = __ldg(f + size_t(min(k0 + j, nz - 1)) * nc + c);
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    const int k = k0 + j;
+                    if (k < nz) {
+                        const float rf =
+                            __fmul_rn(__fmul_rn(A32, __ldg(e32.V + k)), f64_to_f32_rn(fv[j]));
+                        if (MODE == 1) r32[size_t(k) * nc + c] = rf * sc;
+                        colsum = fmaf(rf, rf, colsum);
+                    }
+                }
             }
         } else {
             // FP64 is the scarce unit here (about 11 FP64 instructions per
@@ -1436,10 +1449,20 @@ __global__ void __launch_bounds__(kBlk) k_ir_update(const Lv<double> *__restrict
     const long long sb = __double_as_longlong(scale[it.lv]);
     const int k = 1023 - static_cast<int>((sb >> 52) & 0x7ff);
     if ((sb & ((1ll << 52) - 1)) == 0 && sb > 0) {
-#pragma unroll 8
-        for (int l = 0; l < d.nz; ++l) {
-            const size_t o = size_t(l) * nc + c;
-            x[o] += f32_to_f64_pow2(__ldg(e + o), k);
+        // eight levels' loads are issued before their conversions
+        constexpr int B = 8;
+        for (int l0 = 0; l0 < d.nz; l0 += B) {
+            float ev[B];
+            double xv[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const size_t o = size_t(min(l0 + j, d.nz - 1)) * nc + c;
+                ev[j] = __ldg(e + o);
+                xv[j] = x[o];
+            }
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (l0 + j < d.nz) x[size_t(l0 + j) * nc + c] = xv[j] + f32_to_f64_pow2(ev[j], k);
         }
     } else {
         const double inv = 1.0 / scale[it.lv];

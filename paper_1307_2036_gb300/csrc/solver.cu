@@ -1187,7 +1187,7 @@ void ellsolve_default_opts(ellsolve_opts *o) {
     o->coarsest_min = 4;
     o->max_levels = 0;
     o->prolong = 0;
-    o->inner_cycles = 2;
+    o->inner_cycles = 3;
     o->use_graph = 1;
 }
 

@@ -30,7 +30,7 @@ def test_sphere512_solve_meets_tolerance_in_oracle_residual(oracle_mod):
     f = inputs.smooth_per_panel(inputs.gaussian(shape, member=0), sweeps=3)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sv = ellsolve.Solver(KIND, N, NZ, r, W2, L2, precision=1, use_graph=1, inner_cycles=2,
+        sv = ellsolve.Solver(KIND, N, NZ, r, W2, L2, precision=1, use_graph=1, inner_cycles=3,
                              stream=stream.cuda_stream)
         fd = torch.from_numpy(f).to("cuda")
         x = torch.zeros_like(fd)
