@@ -1301,6 +1301,191 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// Residual fused with the restriction, row-staged (FP32, fine n % 64 == 0).
+// A warp takes 32 coarse columns of one coarse row J: the 2 x 2 children of
+// each lie in fine rows 2J and 2J+1, 64 fine columns wide.  Per level it
+// stages with aligned 16-byte cp.async copies the two child rows with one
+// halo column each side, the fine rows 2J-1 and 2J+2, and the two rows of b
+// (100 chunks) into a kRR-level ring; the children's own values are carried
+// in registers from one level to the next.  Neighbours across a panel edge
+// (the west halo of lane 0, the east halo of lane 31, a whole row 2J-1 or
+// 2J+2) come from the neighbour table and are copied into the ring positions
+// of the chunks they replace.  Each child pair of a fine row is one FP32x2
+// operand.
+// ---------------------------------------------------------------------------
+constexpr int kRR = 4;                              // ring depth (levels)
+constexpr int kRsF = 400;                           // floats per warp and level
+constexpr int kR0 = 0, kR1 = 72, kRm = 144, kRp = 208, kRb0 = 272, kRb1 = 336;
+
+__host__ __device__ inline size_t restrict_rows_smem_bytes() {
+    return size_t(kRR) * (kBlk / 32) * kRsF * 4;
+}
+
+__global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restrict__ L,
+                                                        const Item *__restrict__ items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>(smem_raw);
+    const Item it = items[blockIdx.x];
+    const Lv<float> &d = L[it.lv];
+    const Lv<float> &dc = L[it.lv + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int C = it.col0 + threadIdx.x;
+    const int ncc = dc.ncol, ncn = dc.n;
+    const int nz = d.nz, nf = d.n, nc = d.ncol;
+    const bool active = C < ncc;  // whole warps: ncc % 32 == 0
+    const int Cw = it.col0 + 32 * warp;
+    if (Cw >= ncc) return;  // a warp with no column (no block-wide barrier follows)
+    const int I = C % ncn, t = C / ncn, J = t % ncn, p = t / ncn;
+    const int f0 = (p * nf + 2 * J) * nf + 2 * I;  // child (2I, 2J)
+    const int fw = f0 - 2 * lane;                   // child (2 I0, 2J) of lane 0
+    const float *__restrict__ u = d.u[it.in];
+    const float *__restrict__ b = d.b;
+    float *__restrict__ bc = dc.b;
+    const size_t snc = size_t(nc);
+    // children 0 (2I, 2J), 1 (2I+1, 2J), 2 (2I, 2J+1), 3 (2I+1, 2J+1)
+    const Column<float> c0 = load_column(d, f0), c1 = load_column(d, f0 + 1),
+                        c2 = load_column(d, f0 + nf), c3 = load_column(d, f0 + nf + 1);
+    // Off-row neighbours, decided per staged row and warp-uniform.  A chunk is
+    // replaced when any of its neighbours is not the cell next to it in the
+    // layout; the replacement then takes every value from the neighbour table,
+    // which is right also where an off-row neighbour's index happens to equal
+    // the next cell's (the west neighbour of cell (0, 0) of panel 4 is the
+    // last cell of panel 3).  The rows 2J and 2J+1 are decided separately.
+    const bool fb_w0 = __shfl_sync(0xffffffffu, c0.nb.x != f0 - 1, 0);
+    const bool fb_w2 = __shfl_sync(0xffffffffu, c2.nb.x != f0 + nf - 1, 0);
+    const bool fb_e1 = __shfl_sync(0xffffffffu, c1.nb.y != f0 + 2, 31);
+    const bool fb_e3 = __shfl_sync(0xffffffffu, c3.nb.y != f0 + nf + 2, 31);
+    const bool fb_s = __any_sync(0xffffffffu, c0.nb.z != f0 - nf || c1.nb.z != f0 + 1 - nf);
+    const bool fb_n =
+        __any_sync(0xffffffffu, c2.nb.w != f0 + 2 * nf || c3.nb.w != f0 + 2 * nf + 1);
+
+    // chunk q of a level's 100: 0..17 row 2J with halo, 18..35 row 2J+1 with
+    // halo, 36..51 row 2J-1, 52..67 row 2J+2, 68..83 b row 2J, 84..99 b row 2J+1
+    auto chunk = [&](int q, const float *&src, int &dst, bool &iss) {
+        const float *base = u;
+        int scol;
+        bool skip = false;
+        if (q < 18) {
+            scol = fw - 4 + 4 * q; dst = kR0 + 4 * q;
+            skip = (q == 0 && fb_w0) || (q == 17 && fb_e1);
+        } else if (q < 36) {
+            scol = fw + nf - 4 + 4 * (q - 18); dst = kR1 + 4 * (q - 18);
+            skip = (q == 18 && fb_w2) || (q == 35 && fb_e3);
+        } else if (q < 52) {
+            scol = fw - nf + 4 * (q - 36); dst = kRm + 4 * (q - 36); skip = fb_s;
+        } else if (q < 68) {
+            scol = fw + 2 * nf + 4 * (q - 52); dst = kRp + 4 * (q - 52); skip = fb_n;
+        } else if (q < 84) {
+            base = b; scol = fw + 4 * (q - 68); dst = kRb0 + 4 * (q - 68);
+        } else {
+            base = b; scol = fw + nf + 4 * (q - 84); dst = kRb1 + 4 * (q - 84);
+        }
+        iss = q < 100 && !skip && scol >= 0 && scol + 4 <= nc;
+        src = iss ? base + scol : b;
+    };
+    const float *pq[4];
+    int dq[4];
+    bool iq[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) chunk(lane + 32 * r, pq[r], dq[r], iq[r]);
+    // this lane's replacement values: column index and ring position (W of
+    // children 0, 2 on lane 0 / E of 1, 3 on lane 31; S of 0, 1 or N of 2, 3)
+    int fa = -1, fb2 = -1, pa = 0, pb = 0;
+    if (lane == 0 && fb_w0) { fa = c0.nb.x; pa = kR0 + 3; }
+    if (lane == 0 && fb_w2) { fb2 = c2.nb.x; pb = kR1 + 3; }
+    if (lane == 31 && fb_e1) { fa = c1.nb.y; pa = kR0 + 68; }
+    if (lane == 31 && fb_e3) { fb2 = c3.nb.y; pb = kR1 + 68; }
+    int fs0 = -1, fs1 = -1, ps = 0;
+    if (fb_s) { fs0 = c0.nb.z; fs1 = c1.nb.z; ps = kRm + 2 * lane; }
+    if (fb_n) { fs0 = c2.nb.w; fs1 = c3.nb.w; ps = kRp + 2 * lane; }
+    float *wring = ring + warp * kRsF;
+    constexpr int kStride = (kBlk / 32) * kRsF;
+
+    auto issue = [&](int k) {
+        float *sl = wring + (k % kRR) * kStride;
+        if (k < nz) {
+            const size_t o = size_t(k) * snc;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (iq[r]) cp_async16(sl + dq[r], pq[r] + o, 16);
+            if (fa >= 0) cp_async(sl + pa, u + o + fa, true);
+            if (fb2 >= 0) cp_async(sl + pb, u + o + fb2, true);
+            if (fs0 >= 0) {
+                cp_async(sl + ps, u + o + fs0, true);
+                cp_async(sl + ps + 1, u + o + fs1, true);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < kRR - 1; ++k) issue(k);
+
+    const int o0 = 4 + 2 * lane;  // this lane's child pair in the halo rows
+    const float2 A01 = make_float2(c0.A, c1.A), A23 = make_float2(c2.A, c3.A);
+    const float2 tw01 = make_float2(c0.t0, c1.t0), te01 = make_float2(c0.t1, c1.t1),
+                 ts01 = make_float2(c0.t2, c1.t2), tn01 = make_float2(c0.t3, c1.t3);
+    const float2 tw23 = make_float2(c2.t0, c3.t0), te23 = make_float2(c2.t1, c3.t1),
+                 ts23 = make_float2(c2.t2, c3.t2), tn23 = make_float2(c2.t3, c3.t3);
+    cp_async_wait<kRR - 2>();
+    __syncwarp();
+    float2 u01 = *reinterpret_cast<const float2 *>(wring + kR0 + o0);
+    float2 u23 = *reinterpret_cast<const float2 *>(wring + kR1 + o0);
+    float2 m01 = f2(0.f), m23 = f2(0.f);
+    float gk = d.g[0];
+#pragma unroll 1
+    for (int k = 0; k < nz; ++k) {
+        __syncwarp();
+        issue(k + kRR - 1);
+        cp_async_wait<kRR - 2>();
+        __syncwarp();
+        const float *sk = wring + (k % kRR) * kStride;
+        const float *sn = wring + ((k + 1) % kRR) * kStride;
+        const float gk1 = d.g[k + 1], Vk = d.V[k];
+        float2 p01 = f2(0.f), p23 = f2(0.f);
+        if (k + 1 < nz) {
+            p01 = *reinterpret_cast<const float2 *>(sn + kR0 + o0);
+            p23 = *reinterpret_cast<const float2 *>(sn + kR1 + o0);
+        }
+        const float2 b01 = *reinterpret_cast<const float2 *>(sk + kRb0 + 2 * lane);
+        const float2 b23 = *reinterpret_cast<const float2 *>(sk + kRb1 + 2 * lane);
+        const float2 s01 = *reinterpret_cast<const float2 *>(sk + kRm + 2 * lane);
+        const float2 n23 = *reinterpret_cast<const float2 *>(sk + kRp + 2 * lane);
+        const float2 w01 = make_float2(sk[kR0 + o0 - 1], u01.x);
+        const float2 e01 = make_float2(u01.y, sk[kR0 + o0 + 2]);
+        const float2 w23 = make_float2(sk[kR1 + o0 - 1], u23.x);
+        const float2 e23 = make_float2(u23.y, sk[kR1 + o0 + 2]);
+        // children 0, 1: north neighbours are children 2, 3; children 2, 3:
+        // south neighbours are children 0, 1
+        float2 h01 = __fmul2_rn(tw01, sub2(u01, w01));
+        h01 = __ffma2_rn(te01, sub2(u01, e01), h01);
+        h01 = __ffma2_rn(ts01, sub2(u01, s01), h01);
+        h01 = __ffma2_rn(tn01, sub2(u01, u23), h01);
+        float2 h23 = __fmul2_rn(tw23, sub2(u23, w23));
+        h23 = __ffma2_rn(te23, sub2(u23, e23), h23);
+        h23 = __ffma2_rn(ts23, sub2(u23, u01), h23);
+        h23 = __ffma2_rn(tn23, sub2(u23, n23), h23);
+        float2 v01 = __fmul2_rn(f2(gk1), sub2(u01, p01));
+        v01 = __ffma2_rn(f2(gk), sub2(u01, m01), v01);
+        float2 v23 = __fmul2_rn(f2(gk1), sub2(u23, p23));
+        v23 = __ffma2_rn(f2(gk), sub2(u23, m23), v23);
+        float2 a01 = __fmul2_rn(A01, __fmul2_rn(f2(Vk), u01));
+        a01 = __ffma2_rn(f2(Vk), h01, a01);
+        a01 = __ffma2_rn(A01, v01, a01);
+        float2 a23 = __fmul2_rn(A23, __fmul2_rn(f2(Vk), u23));
+        a23 = __ffma2_rn(f2(Vk), h23, a23);
+        a23 = __ffma2_rn(A23, v23, a23);
+        const float2 r = __fadd2_rn(sub2(b01, a01), sub2(b23, a23));
+        if (active) bc[size_t(k) * ncc + C] = r.x + r.y;
+        m01 = u01;
+        m23 = u23;
+        u01 = p01;
+        u23 = p23;
+        gk = gk1;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Prolongation and coarse-grid correction (Algorithm 1; Sec. 6.2.1 linear
 // interpolation): cell-centred bilinear weights 9/16, 3/16, 3/16, 1/16; where
 // three cells meet at a cube corner, 1/2, 1/4, 1/4.  The loads of kPB levels
@@ -1797,6 +1982,16 @@ cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *it
     cudaError_t e = set_smem(k_restrict_resid<T>, bytes);
     if (e != cudaSuccess) return e;
     k_restrict_resid<T><<<nitems, kBlk, bytes, s>>>(L, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item *items,
+                                 int nitems) {
+    if (nitems <= 0) return cudaSuccess;
+    const size_t bytes = restrict_rows_smem_bytes();
+    cudaError_t e = set_smem(k_restrict_rows, bytes);
+    if (e != cudaSuccess) return e;
+    k_restrict_rows<<<nitems, kBlk, bytes, s>>>(L, items);
     return cudaGetLastError();
 }
 

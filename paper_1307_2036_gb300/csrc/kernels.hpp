@@ -57,6 +57,10 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 //   L32[m].b = float(r * scale[m]), partials[item] = sum of r^2.
 // x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve);
 // 2 the same but only the norm (r32 is not written).
+// Row-staged FP32 residual + restriction; every fine level of the launch has
+// n % 64 == 0.
+cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item *items,
+                                 int nitems);
 cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned long long *bad);
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,

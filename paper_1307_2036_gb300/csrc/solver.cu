@@ -475,16 +475,27 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
         if (o.nu_coarse == 0) emit_memsets(coarse);
         if (!pre.empty()) {
             emit_memsets(pre);
-            Op op;
-            op.kind = Op::kRestrict;
-            op.off = int(items.size());
-            for (auto [m, l] : pre) {
-                push_items(items, base[m] + l, mem[m]->lev[l + 1].ncol, st[m].cur[l], 0, 0);
-                st[m].zero[l + 1] = 1;  // the coarse iterate starts from zero
-                st[m].cur[l + 1] = 0;
+            // one launch for the levels the row-staged kernel takes, one for the rest
+            std::vector<std::pair<int, int>> rows_pre, other_pre;
+            for (auto ml : pre)
+                (precision == 1 && restrict_rows_eligible(*mem[ml.first], ml.second) ? rows_pre
+                                                                                     : other_pre)
+                    .push_back(ml);
+            for (int pass = 0; pass < 2; ++pass) {
+                const auto &list = pass == 0 ? rows_pre : other_pre;
+                if (list.empty()) continue;
+                Op op;
+                op.kind = Op::kRestrict;
+                op.rows_ok = pass == 0;
+                op.off = int(items.size());
+                for (auto [m, l] : list) {
+                    push_items(items, base[m] + l, mem[m]->lev[l + 1].ncol, st[m].cur[l], 0, 0);
+                    st[m].zero[l + 1] = 1;  // the coarse iterate starts from zero
+                    st[m].cur[l + 1] = 0;
+                }
+                op.n = int(items.size()) - op.off;
+                prog.ops.push_back(op);
             }
-            op.n = int(items.size()) - op.off;
-            prog.ops.push_back(op);
         }
     }
     // up the V: prolongation, correction and post-smoothing
@@ -523,6 +534,10 @@ void Plan::sync_items() {
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
+bool restrict_rows_eligible(const Problem &p, int level) {
+    return level + 1 < p.nlev && p.lev[level].n % 64 == 0;
+}
+
 bool rows_eligible(const Problem &p, int level) {
     const LevelStore &Ls = p.lev[level];
     if (Ls.n % 4 != 0 || Ls.ncol % 4 != 0) return false;
@@ -585,7 +600,12 @@ static void run_program(Plan &pl, const Program &prog) {
                 break;
             }
             case Op::kRestrict:
-                check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n), "restrict");
+                if (sizeof(T) == 4 && op.rows_ok)
+                    check_cuda(launch_restrict_rows(s, reinterpret_cast<const Lv<float> *>(L),
+                                                    it + op.off, op.n),
+                               "restrict_rows");
+                else
+                    check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n), "restrict");
                 count(pl);
                 break;
             case Op::kProlong:
@@ -1142,8 +1162,13 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
             break;
         }
         case 3:
-            check_cuda(launch_restrict_resid<T>(s, L, it, div_up(p.lev[level + 1].ncol, kBlk)),
-                       "restrict");
+            if (sizeof(T) == 4 && restrict_rows_eligible(p, level))
+                check_cuda(launch_restrict_rows(s, reinterpret_cast<const Lv<float> *>(L), it,
+                                                div_up(p.lev[level + 1].ncol, kBlk)),
+                           "restrict_rows");
+            else
+                check_cuda(launch_restrict_resid<T>(s, L, it, div_up(p.lev[level + 1].ncol, kBlk)),
+                           "restrict");
             break;
         case 4: check_cuda(launch_prolong_add<T>(s, L, it, per, p.opts.prolong), "prolong"); break;
     }

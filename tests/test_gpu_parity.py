@@ -128,6 +128,44 @@ def test_kernels_fp32(torch_mod, oracle_mod, case):
             assert rel_l2(p.host(uf), p.og.prolong_add(uc, u, lev)) <= 1e-6
 
 
+# Levels with n % 32 == 0 (the line smoother's aligned variant: panel-edge
+# neighbours written into its staging ring) and n % 64 == 0 (the row-staged
+# restriction), on the sphere with both mappings and on the periodic box.
+ALIGNED = [
+    (1, 64, 16, True, 0, 0.01, 1.0),
+    (1, 128, 8, False, 1, 0.05, 4.0),
+    (0, 128, 16, True, 0, 0.02, 0.25),
+]
+AIDS = ["sph64", "sph128e", "box128"]
+
+
+@pytest.mark.parametrize("case", ALIGNED, ids=AIDS)
+def test_aligned_kernels_fp32(torch_mod, oracle_mod, case):
+    p = make(oracle_mod, case, precision=1)
+    for lev in range(min(2, p.og.nlevels - 1)):
+        u = f32exact(rand(p.og.shape(lev), 170 + lev))
+        b = f32exact(p.og.volumes(lev) * rand(p.og.shape(lev), 180 + lev))
+        bc = p.empty(lev + 1, fp32=True)
+        p.sv.level_restrict_residual(lev, p.dev(b, True), p.dev(u, True), bc, fp32=True)
+        ref = p.og.restrict(p.og.residual(b, u, lev), lev)
+        got = p.host(bc)
+        assert rel_l2(got, ref) <= 1e-5, lev
+        # element by element as well: a wrong neighbour in one column (a panel
+        # corner) hardly moves the L2 norm over thousands of columns
+        assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref)), lev
+        uh = f32exact(np.broadcast_to(rand(p.og.shape(lev)[1:], 175 + lev), p.og.shape(lev)))
+        ud = p.dev(uh, True)
+        p.sv.level_smooth(lev, p.dev(b, True), ud, nsweeps=2, rho=0.8, fp32=True)
+        sref = p.og.smooth(b, uh, 2, 0.8, lev)
+        sgot = p.host(ud)
+        assert rel_l2(sgot, sref) <= 1e-5, lev
+        assert np.max(np.abs(sgot - sref)) <= 2e-5 * np.max(np.abs(sref)), lev
+        uc = f32exact(rand(p.og.shape(lev + 1), 190 + lev))
+        uf = p.dev(u, True)
+        p.sv.level_prolong_add(lev, p.dev(uc, True), uf, fp32=True)
+        assert rel_l2(p.host(uf), p.og.prolong_add(uc, u, lev)) <= 1e-6, lev
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_vcycles_fp64_fixed_count(torch_mod, oracle_mod, case):
     p = make(oracle_mod, case)
