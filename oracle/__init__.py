@@ -45,6 +45,10 @@ def _load():
             "og_thomas_excess": (None, [C.c_int, dp, dp, dp, dp, dp]),
             "og_smooth": (None, [vp, C.c_int, dp, dp, C.c_int, C.c_double]),
             "og_line_precond": (None, [vp, C.c_int, dp, dp]),
+            "og_smooth_rb": (None, [vp, C.c_int, dp, dp, C.c_int, C.c_double]),
+            "og_rb_ssor": (None, [vp, C.c_int, dp, dp, C.c_double]),
+            "og_set_smoother": (None, [vp, C.c_int]),
+            "og_set_precond": (None, [vp, C.c_int, C.c_double]),
             "og_restrict": (None, [vp, C.c_int, dp, dp]),
             "og_prolong_add": (None, [vp, C.c_int, dp, dp, C.c_int]),
             "og_vcycle": (None, [vp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -91,7 +95,9 @@ class Grid:
     horizontal multigrid hierarchy (level 0 finest)."""
 
     def __init__(self, kind, n, nz, r, omega2, lambda2, mapping=0, side=2 * np.pi,
-                 coarsest_min=4, max_levels=0):
+                 coarsest_min=4, max_levels=0, smoother=0, precond=0, precond_rho=1.0):
+        """smoother: 0 block Jacobi, 1 block red-black SOR (smooth, vcycle,
+        mg_solve); precond: 0 block Jacobi, 1 block red-black SSOR (pcg_solve)."""
         lib = _load()
         r = _f64(r)
         assert r.shape == (nz + 1,)
@@ -99,6 +105,8 @@ class Grid:
         self.omega2, self.lambda2 = omega2, lambda2
         self._h = lib.og_create(kind, n, nz, mapping, side, _dp(r), omega2, lambda2,
                                 coarsest_min, max_levels)
+        lib.og_set_smoother(self._h, smoother)
+        lib.og_set_precond(self._h, precond, precond_rho)
         self.P = lib.og_npanel(self._h)
         self.nlevels = lib.og_nlevels(self._h)
 
@@ -177,6 +185,19 @@ class Grid:
         u = _f64(u).reshape(self.shape(lev)).copy()
         _load().og_smooth(self._h, lev, _dp(b), _dp(u), nsweeps, rho)
         return u
+
+    def rb_ssor(self, r, rho=1.0, lev=0):
+        """z = M^{-1} r of the block red-black SSOR preconditioner."""
+        r = _f64(r).reshape(self.shape(lev))
+        z = np.empty_like(r)
+        _load().og_rb_ssor(self._h, lev, _dp(r), _dp(z), rho)
+        return z
+
+    def colour(self, lev=0):
+        """0 (red) or 1 (black) per column: parity of i + j."""
+        n = self.level_n(lev)
+        c = np.arange(self.ncol(lev))
+        return ((c % n) + (c // n) % n) % 2
 
     def line_precond(self, r, lev=0):
         r = _f64(r).reshape(self.shape(lev))

@@ -37,6 +37,9 @@ typedef struct {
 
 struct og_grid {
     int kind, P, nz, mapping, nlev;
+    int smoother;        /* 0 block Jacobi, 1 block red-black SOR */
+    int precond;         /* PCG: 0 block Jacobi, 1 block red-black SSOR */
+    double precond_rho;  /* relaxation parameter of the SSOR preconditioner */
     double side, omega2, lambda2;
     double *r, *V, *G;  /* r[nz+1], V[nz], G[nz+1] */
     og_level lev[MAXLEV];
@@ -184,6 +187,9 @@ og_grid *og_create(int kind, int n, int nz, int mapping, double side, const doub
                    double omega2, double lambda2, int coarsest_min, int max_levels)
 {
     og_grid *g = (og_grid *)calloc(1, sizeof(og_grid));
+    g->smoother = 0;
+    g->precond = 0;
+    g->precond_rho = 1.0;
     g->kind = kind;
     g->P = kind == 0 ? 1 : 6;
     g->nz = nz;
@@ -424,8 +430,87 @@ static void og_column_solve(const og_grid *g, const og_level *L, long c, const d
     free(lo);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Block red-black SOR (Sec. 4.2, Eq. BlockRBSOR): a column is red when the   */
+/* sum i + j of its horizontal indices is even and black otherwise (Sec.      */
+/* 6.2.1).  One sweep updates the red columns, then the black ones:           */
+/*   u_c <- u_c + rho Dtilde_c^{-1} (b - A u)_c   for every column c of the   */
+/* colour, the residual taken with the current iterate.  On the periodic box  */
+/* (n even) no two columns of one colour are neighbours.  On the cubed sphere */
+/* that cannot hold everywhere (three cells meet pairwise at a cube corner):  */
+/* columns of one colour are updated together, so a same-colour neighbour     */
+/* enters with its value from before the half-sweep.                          */
+/* ------------------------------------------------------------------------ */
+static int og_colour(const og_level *L, long c)
+{
+    long n = L->n;
+    return (int)(((c % n) + (c / n) % n) & 1);
+}
+
+static void og_half_sweep(const og_grid *g, int lev, const double *b, double *u, int colour,
+                          double rho)
+{
+    const og_level *L = &g->lev[lev];
+    long nc = L->ncol, N = nc * g->nz;
+    int nz = g->nz;
+    double *r = (double *)malloc(N * sizeof(double));
+    double *col_r = (double *)malloc(nz * sizeof(double));
+    double *col_e = (double *)malloc(nz * sizeof(double));
+    og_residual(g, lev, b, u, r);
+    for (long c = 0; c < nc; ++c) {
+        if (og_colour(L, c) != colour) continue;
+        for (int k = 0; k < nz; ++k) col_r[k] = r[k * nc + c];
+        og_column_solve(g, L, c, col_r, col_e);
+        for (int k = 0; k < nz; ++k) u[k * nc + c] += rho * col_e[k];
+    }
+    free(r);
+    free(col_r);
+    free(col_e);
+}
+
+void og_set_smoother(og_grid *g, int kind) { g->smoother = kind; }
+
+void og_set_precond(og_grid *g, int kind, double rho)
+{
+    g->precond = kind;
+    g->precond_rho = rho;
+}
+
+void og_smooth_rb(const og_grid *g, int lev, const double *b, double *u, int nsweeps, double rho)
+{
+    for (int s = 0; s < nsweeps; ++s) {
+        og_half_sweep(g, lev, b, u, 0, rho);
+        og_half_sweep(g, lev, b, u, 1, rho);
+    }
+}
+
+/* Block red-black SSOR as the CG preconditioner (Sec. 7.2): z = M^{-1} r is
+ * the result of a forward sweep (red, black) and a backward sweep (black,
+ * red) of Au = r from u = 0.  Each half-sweep is symmetric in the A inner
+ * product, so the sequence red, black, black, red gives a symmetric M. */
+void og_rb_ssor(const og_grid *g, int lev, const double *r, double *z, double rho)
+{
+    long N = g->lev[lev].ncol * g->nz;
+    memset(z, 0, N * sizeof(double));
+    og_half_sweep(g, lev, r, z, 0, rho);
+    og_half_sweep(g, lev, r, z, 1, rho);
+    og_half_sweep(g, lev, r, z, 1, rho);
+    og_half_sweep(g, lev, r, z, 0, rho);
+}
+
+void og_line_precond(const og_grid *g, int lev, const double *r, double *z);
+static void og_precond(const og_grid *g, const double *r, double *z)
+{
+    if (g->precond == 1) og_rb_ssor(g, 0, r, z, g->precond_rho);
+    else og_line_precond(g, 0, r, z);
+}
+
 void og_smooth(const og_grid *g, int lev, const double *b, double *u, int nsweeps, double rho)
 {
+    if (g->smoother == 1) {
+        og_smooth_rb(g, lev, b, u, nsweeps, rho);
+        return;
+    }
     const og_level *L = &g->lev[lev];
     long nc = L->ncol, N = nc * g->nz;
     int nz = g->nz;
@@ -584,7 +669,8 @@ int og_mg_solve(const og_grid *g, const double *b, double *u, double rtol, int m
     return it;
 }
 
-/* Algorithm PCG with M = Dtilde (block Jacobi over vertical columns). */
+/* Algorithm PCG with M = Dtilde (block Jacobi over vertical columns) or the
+ * block red-black SSOR preconditioner (og_set_precond). */
 int og_pcg_solve(const og_grid *g, const double *b, double *u, double rtol, int maxit, double *hist)
 {
     long N = g->lev[0].ncol * g->nz;
@@ -594,7 +680,7 @@ int og_pcg_solve(const og_grid *g, const double *b, double *u, double rtol, int 
     double *q = (double *)malloc(N * sizeof(double));
     memset(u, 0, N * sizeof(double));
     og_residual(g, 0, b, u, r);
-    og_line_precond(g, 0, r, z);
+    og_precond(g, r, z);
     memcpy(p, z, N * sizeof(double));
     double kappa_old = og_dot(r, z, N);
     double r0 = og_norm(r, N);
@@ -611,7 +697,7 @@ int og_pcg_solve(const og_grid *g, const double *b, double *u, double rtol, int 
             double rel = og_norm(r, N) / r0;
             if (hist) hist[K] = rel;
             if (rel < rtol) break;
-            og_line_precond(g, 0, r, z);
+            og_precond(g, r, z);
             double kappa = og_dot(r, z, N);
             double beta = kappa / kappa_old;
             for (long m = 0; m < N; ++m) p[m] = z[m] + beta * p[m];

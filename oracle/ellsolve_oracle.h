@@ -64,6 +64,18 @@ void og_smooth(const og_grid *g, int lev, const double *b, double *u, int nsweep
 /* z = Dtilde^{-1} r (the block-Jacobi preconditioner). */
 void og_line_precond(const og_grid *g, int lev, const double *r, double *z);
 
+/* Block red-black SOR (Eq. BlockRBSOR): red columns (i + j even), then black,
+ * each column of the colour updated from the current iterate; in place. */
+void og_smooth_rb(const og_grid *g, int lev, const double *b, double *u, int nsweeps, double rho);
+/* z = M^{-1} r for block red-black SSOR: half-sweeps red, black, black, red of
+ * A z = r from z = 0. */
+void og_rb_ssor(const og_grid *g, int lev, const double *r, double *z, double rho);
+/* Smoother of og_smooth / og_vcycle / og_mg_solve: 0 block Jacobi (default),
+ * 1 block red-black SOR.  Preconditioner of og_pcg_solve: 0 block Jacobi
+ * (default), 1 block red-black SSOR with parameter rho. */
+void og_set_smoother(og_grid *g, int kind);
+void og_set_precond(og_grid *g, int kind, double rho);
+
 /* Intergrid transfers between level lev_f and lev_f + 1. */
 void og_restrict(const og_grid *g, int lev_f, const double *r_f, double *b_c);
 void og_prolong_add(const og_grid *g, int lev_f, const double *u_c, double *u_f, int mode);
