@@ -80,6 +80,13 @@ typedef struct {
     int prolong;      /* 0: bilinear (cell-centred), 1: piecewise constant */
     int inner_cycles; /* precision 1: FP32 V-cycles per FP64 refinement step (3) */
     int use_graph;    /* 1: replay the per-iteration work as a CUDA graph */
+    int smoother;     /* 0: damped block (line) Jacobi; 1: block red-black SOR (Eq.
+                       * BlockRBSOR) with rho = damping, a sweep being a red then a
+                       * black half-sweep; a column is red when i + j is even.  On
+                       * the cubed sphere, which has no two-colouring, a half-sweep
+                       * updates its columns from the iterate before it (0) */
+    int precond;      /* PCG: 0 block Jacobi Dtilde^{-1}; 1 block red-black SSOR
+                       * (half-sweeps red, black, black, red from 0, rho = 1) (0) */
 } ellsolve_opts;
 
 typedef struct {

@@ -37,8 +37,14 @@ struct Lv {
 struct Item {
     int lv;
     int col0;
-    unsigned char in, out, zero, pad;
+    // colour: 0 every column (line Jacobi); 1 only red columns (i + j even),
+    // 2 only black ones (block red-black SOR half-sweep) -- a smoother copies
+    // the columns of the other colour from `in` to `out` unchanged
+    unsigned char in, out, zero, colour;
 };
+
+// 0 red (i + j even), 1 black, for column c of a level with n x n cells per panel
+__host__ __device__ inline int column_colour(int c, int n) { return ((c % n) + (c / n) % n) & 1; }
 
 constexpr int kBlk = 128;
 

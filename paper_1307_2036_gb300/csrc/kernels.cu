@@ -188,6 +188,14 @@ __global__ void __launch_bounds__(kBlk) k_smooth(const Lv<T> *__restrict__ L,
     const bool zero = ZERO == 2 ? (it.zero != 0) : (ZERO == 1);
     const T *__restrict__ u = d.u[it.in];
     T *__restrict__ un = d.u[it.out];
+    if (it.colour && column_colour(c, d.n) != it.colour - 1) {
+        // red-black half-sweep: a column of the other colour is carried over
+        for (int k = 0; k < nz; ++k) {
+            const size_t o = size_t(k) * nc + c;
+            un[o] = zero ? T(0) : u[o];
+        }
+        return;
+    }
     const T *__restrict__ b = d.b;
     const T *__restrict__ V = d.V;
     const T *__restrict__ g = d.g;
@@ -872,6 +880,10 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     const int c = it.col0 + tid;
     const int c0w = it.col0 + 32 * warp;
     const bool active = c < nc;
+    // red-black half-sweep: a column of the other colour is carried over (its
+    // lane still runs the elimination, in step with the warp, but stores the
+    // iterate it read instead)
+    const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
     constexpr bool zero = ZERO == 1;
     for (int i = tid; i < m; i += kTT) {
         VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
@@ -1027,6 +1039,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             const float *sk = wring + j * kStride;
             float2 r = make_float2(sk[kBT + lane], sk[kLvF + kBT + lane]);
             const float2 hi_g = GH[s], Vp = VP[s];
+            const float2 ucur = u0;  // the iterate at levels k, k' (carried over when !upd)
             if (!zero) {
                 float2 up;
                 if (last && j == FR - 1) {
@@ -1065,8 +1078,8 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             pv = pivot2(__fmul2_rn(Vp, f2(sv)), lo, hi, ratio);
             fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
             if (active) {
-                *fpb = fp.x;
-                *fpt = fp.y;
+                *fpb = upd ? fp.x : ucur.x;
+                *fpt = upd ? fp.y : ucur.y;
             }
             fpb += snc;
             fpt -= snc;
@@ -1139,7 +1152,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             const float2 uo = zero ? f2(0.f) : make_float2(sk[64 + lane], sk[96 + lane]);
             if (s != m - 1) x = __ffma2_rn(cpr[jj], x, fk);
             const float2 un2 = __ffma2_rn(f2(rho), x, uo);
-            if (active) {
+            if (active && upd) {
                 __stcs(uob, un2.x);
                 __stcs(uot, un2.y);
             }
@@ -1802,6 +1815,25 @@ __global__ void __launch_bounds__(kBlk) k_cg_precond_dot(const Lv<double> *__res
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
+// <x, y> over the columns of each item, one partial per block (fixed order)
+__global__ void __launch_bounds__(kBlk) k_dot(const Lv<double> *__restrict__ L,
+                                              const Item *__restrict__ items,
+                                              const double *__restrict__ x,
+                                              const double *__restrict__ y,
+                                              double *__restrict__ partials) {
+    const Item it = items[blockIdx.x];
+    const Lv<double> &d = L[it.lv];
+    const int c = it.col0 + threadIdx.x;
+    double acc = 0.0;
+    if (c < d.ncol)
+        for (int k = 0; k < d.nz; ++k) {
+            const size_t o = size_t(k) * d.ncol + c;
+            acc = fma(__ldg(x + o), __ldg(y + o), acc);
+        }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
 __global__ void k_cg_xpay(const double *__restrict__ z, double *__restrict__ p,
                           const double *__restrict__ scalars, size_t n) {
     const double beta = scalars[kBeta];
@@ -2090,6 +2122,13 @@ cudaError_t launch_cg_precond_dot(cudaStream_t s, const Lv<double> *L, const Ite
                                   int nitems, const double *r, double *z, double *scratch,
                                   double *partials) {
     k_cg_precond_dot<<<nitems, kBlk, 0, s>>>(L, items, r, z, scratch, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(cudaStream_t s, const Lv<double> *L, const Item *items, int nitems,
+                      const double *x, const double *y, double *partials) {
+    if (nitems <= 0) return cudaSuccess;
+    k_dot<<<nitems, kBlk, 0, s>>>(L, items, x, y, partials);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,9 @@ cudaError_t launch_cg_precond_dot(cudaStream_t s, const Lv<double> *L, const Ite
                                   int nitems, const double *r, double *z, double *scratch,
                                   double *partials);
 // p = z + beta p, beta = scalars[...] ; n elements
+// partials of <x, y> per item (one per block, deterministic)
+cudaError_t launch_dot(cudaStream_t s, const Lv<double> *L, const Item *items, int nitems,
+                       const double *x, const double *y, double *partials);
 cudaError_t launch_cg_xpay(cudaStream_t s, const double *z, double *p, const double *scalars,
                            size_t n);
 // scalar bookkeeping of Algorithm PCG on the device

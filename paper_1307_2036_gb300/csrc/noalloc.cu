@@ -77,6 +77,9 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
     d.u[0] = static_cast<T *>(u);
     d.u[1] = reinterpret_cast<T *>(base + off_part);
     d.aux = reinterpret_cast<T *>(base + off_aux);
+    // block red-black SOR: a sweep is two half-sweeps, red from the iterate
+    // into the partner buffer, then black back (the parity fixes the colour)
+    const bool rb = p.opts.smoother == 1;
     std::vector<Item> items(size_t(2) * per);
     for (int parity = 0; parity < 2; ++parity)
         for (int i = 0; i < per; ++i) {
@@ -86,7 +89,7 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
             it.in = (unsigned char)parity;
             it.out = (unsigned char)(1 - parity);
             it.zero = 0;
-            it.pad = 0;
+            it.colour = (unsigned char)(rb ? parity + 1 : 0);
         }
     cudaStream_t s = p.stream;
     // pageable sources: the copies are staged by the driver, nothing is allocated
@@ -97,10 +100,11 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
     const Lv<T> *L = reinterpret_cast<const Lv<T> *>(base);
     const Item *it = reinterpret_cast<const Item *>(base + off_items);
     const bool rows = sizeof(T) == 4 && rows_eligible(p, level);
-    for (int sw = 0; sw < nsweeps; ++sw)
+    const int launches = rb ? 2 * nsweeps : nsweeps;
+    for (int sw = 0; sw < launches; ++sw)
         launch_smoother<T>(p, s, L, it + size_t(sw & 1) * per, per, rho, p.nz, 0, rows,
                            p.lev[level].n % 32 == 0);
-    if (nsweeps & 1)
+    if (launches & 1)
         check_cuda(cudaMemcpyAsync(u, d.u[1], nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                    "copy back");
     check_cuda(cudaStreamSynchronize(s), "noalloc sync");

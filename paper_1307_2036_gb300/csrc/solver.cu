@@ -300,7 +300,7 @@ struct MemberState {
     std::vector<char> zero;  // level iterate known to be zero
 };
 
-void push_items(std::vector<Item> &v, int lv, int ncol, int in, int out, int zero) {
+void push_items(std::vector<Item> &v, int lv, int ncol, int in, int out, int zero, int colour = 0) {
     for (int c0 = 0; c0 < ncol; c0 += kBlk) {
         Item it;
         it.lv = lv;
@@ -308,7 +308,7 @@ void push_items(std::vector<Item> &v, int lv, int ncol, int in, int out, int zer
         it.in = (unsigned char)in;
         it.out = (unsigned char)out;
         it.zero = (unsigned char)zero;
-        it.pad = 0;
+        it.colour = (unsigned char)colour;
         v.push_back(it);
     }
 }
@@ -405,7 +405,8 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
     auto lvl_count = [&](int m) { return mem[m]->nlev; };
 
     auto rows_level = [&](int m, int l) { return precision == 1 && rows_eligible(*mem[m], l); };
-    auto emit_smooth_one = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
+    auto emit_smooth_one = [&](const std::vector<std::pair<int, int>> &ml, double rho,
+                               int colour) {
         if (ml.empty()) return;
         Op op;
         op.kind = Op::kSmooth;
@@ -420,7 +421,8 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
             if (mem[m]->lev[l].n % 32 != 0) op.aligned = false;
             MemberState &s = st[m];
             (s.zero[l] ? z_items : nz_items) += 1;
-            push_items(items, base[m] + l, mem[m]->lev[l].ncol, s.cur[l], 1 - s.cur[l], s.zero[l]);
+            push_items(items, base[m] + l, mem[m]->lev[l].ncol, s.cur[l], 1 - s.cur[l], s.zero[l],
+                       colour);
             s.cur[l] ^= 1;
             s.zero[l] = 0;
             op.max_nz = std::max(op.max_nz, mem[m]->nz);
@@ -437,11 +439,34 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
     };
     // one launch for the levels the row-staged kernel takes, one for the rest,
     // so that a member's kernel does not depend on the other members
-    auto emit_smooth = [&](const std::vector<std::pair<int, int>> &ml, double rho) {
-        std::vector<std::pair<int, int>> a, b;
-        for (auto ml1 : ml) (rows_level(ml1.first, ml1.second) ? a : b).push_back(ml1);
-        emit_smooth_one(a, rho);
-        emit_smooth_one(b, rho);
+    // One sweep: a launch for the levels the row-staged kernel takes and one
+    // for the rest, so that a member's kernel does not depend on the other
+    // members; members with the block red-black SOR smoother take two
+    // half-sweeps (red, then black).
+    // Members are grouped by (smoother, damping): each member sweeps with its
+    // own relaxation parameter (the coarsest level undamped, rho = 1).
+    auto emit_smooth = [&](const std::vector<std::pair<int, int>> &ml, bool coarsest) {
+        std::vector<std::pair<int, std::pair<int, double>>> keyed;  // member index, key
+        std::vector<std::pair<int, double>> keys;
+        for (size_t i = 0; i < ml.size(); ++i) {
+            const ellsolve_opts &mo = mem[ml[i].first]->opts;
+            const std::pair<int, double> key{mo.smoother, coarsest ? 1.0 : mo.damping};
+            if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+            keyed.push_back({int(i), key});
+        }
+        for (const auto &key : keys) {
+            std::vector<std::pair<int, int>> group;
+            for (const auto &kv : keyed)
+                if (kv.second == key) group.push_back(ml[kv.first]);
+            const int passes = key.first == 1 ? 2 : 1;
+            for (int pass = 0; pass < passes; ++pass) {
+                const int colour = key.first == 1 ? pass + 1 : 0;
+                std::vector<std::pair<int, int>> a, b;
+                for (auto ml1 : group) (rows_level(ml1.first, ml1.second) ? a : b).push_back(ml1);
+                emit_smooth_one(a, key.second, colour);
+                emit_smooth_one(b, key.second, colour);
+            }
+        }
     };
     auto emit_memsets = [&](const std::vector<std::pair<int, int>> &ml) {
         for (auto [m, l] : ml) {
@@ -469,8 +494,8 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
             std::vector<std::pair<int, int>> a, b;
             if (sw < o.nu_pre) a = pre;
             if (sw < o.nu_coarse) b = coarse;
-            emit_smooth(a, o.damping);
-            emit_smooth(b, 1.0);
+            emit_smooth(a, false);
+            emit_smooth(b, true);
         }
         if (o.nu_coarse == 0) emit_memsets(coarse);
         if (!pre.empty()) {
@@ -511,7 +536,7 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
             push_items(items, base[m] + l, mem[m]->lev[l].ncol, st[m].cur[l + 1], st[m].cur[l], 0);
         op.n = int(items.size()) - op.off;
         prog.ops.push_back(op);
-        for (int sw = 0; sw < o.nu_post; ++sw) emit_smooth(up, o.damping);
+        for (int sw = 0; sw < o.nu_post; ++sw) emit_smooth(up, false);
     }
     prog.fine_cur_out.resize(M);
     for (int m = 0; m < M; ++m) prog.fine_cur_out[m] = st[m].cur[0];
@@ -542,7 +567,8 @@ bool rows_eligible(const Problem &p, int level) {
     const LevelStore &Ls = p.lev[level];
     if (Ls.n % 4 != 0 || Ls.ncol % 4 != 0) return false;
     if (p.smooth_variant == 3) return p.nz % 16 == 0 && smooth_tw_fits(p.nz, 8);
-    return p.nz % 8 == 0 && smooth_rows_fits(p.nz);
+    // the one-sided row kernels have no red-black half-sweeps
+    return p.opts.smoother == 0 && p.nz % 8 == 0 && smooth_rows_fits(p.nz);
 }
 
 template <typename T>
@@ -1028,12 +1054,44 @@ static ellsolve_status solve_pcg(Problem &p, const double *f, double *x, double 
     double *part = pl.partials.as<double>(), *nrm = pl.norms.as<double>();
     const int *first = pl.dfirst.as<int>();
     check_cuda(cudaMemsetAsync(x, 0, N * 8, s), "zero x");
+    // The preconditioner: block Jacobi z = Dtilde^{-1} r (one fused kernel
+    // with <r, z>), or block red-black SSOR (Sec. 7.2): half-sweeps red,
+    // black, black, red of A z = r from z = 0 with rho = 1 (symmetric block
+    // Gauss-Seidel), on the FP64 level-0 buffers the solver does not use
+    // otherwise, then <r, z>.
+    const bool ssor = p.opts.precond == 1;
+    DevBuf sdesc, sitems;
+    const int per0 = div_up(p.lev[0].ncol, kBlk);
+    if (ssor) {
+        std::vector<Lv<double>> hd{p.h64[0]};
+        hd[0].b = r;
+        hd[0].u[0] = z;
+        hd[0].u[1] = p.lev[0].u64[1].as<double>();
+        hd[0].aux = p.lev[0].aux64.as<double>();
+        std::vector<Item> items;
+        const int seq[4][3] = {{0, 1, 1}, {1, 0, 2}, {0, 1, 2}, {1, 0, 1}};  // in, out, colour
+        for (int h = 0; h < 4; ++h)
+            push_items(items, 0, p.lev[0].ncol, seq[h][0], seq[h][1], h == 0 ? 1 : 0, seq[h][2]);
+        upload(sdesc, hd, s);
+        upload(sitems, items, s);
+    }
+    auto precond_dot = [&]() {
+        if (ssor) {
+            for (int h = 0; h < 4; ++h)
+                launch_smoother<double>(p, s, sdesc.as<Lv<double>>(), sitems.as<Item>() + h * per0,
+                                        per0, 1.0, p.nz, h == 0 ? 1 : 0, false, 0);
+            check_cuda(launch_dot(s, L, it, ni, r, z, part), "dot");
+            p.launches += 4;
+        } else {
+            check_cuda(launch_cg_precond_dot(s, L, it, ni, r, z, q, part), "precond");
+        }
+    };
     // r0 = b - A 0 = b
     check_cuda(launch_form_rhs<double>(s, L, it, ni, f, r, part), "form_rhs");
     check_cuda(launch_finalize(s, part, first, 1, nrm, 1, nullptr, nullptr), "finalize");
     const double r0 = read_norms(pl, 1);
     // z0 = M^-1 r0, kappa = <r0, z0>, p0 = z0
-    check_cuda(launch_cg_precond_dot(s, L, it, ni, r, z, q, part), "precond");
+    precond_dot();
     check_cuda(launch_finalize(s, part, first, 1, nrm + 1, 0, nullptr, nullptr), "finalize");
     check_cuda(launch_cg_scalars(s, sc, nrm + 1, 0), "scalars");
     check_cuda(cudaMemcpyAsync(pp, z, N * 8, cudaMemcpyDeviceToDevice, s), "p0");
@@ -1052,7 +1110,7 @@ static ellsolve_status solve_pcg(Problem &p, const double *f, double *x, double 
             rel = read_norms(pl, 1) / r0;
             hist.push_back(rel);
             if (rel < rtol || !std::isfinite(rel)) break;
-            check_cuda(launch_cg_precond_dot(s, L, it, ni, r, z, q, part), "precond");
+            precond_dot();
             check_cuda(launch_finalize(s, part, first, 1, nrm + 1, 0, nullptr, nullptr), "fin");
             check_cuda(launch_cg_scalars(s, sc, nrm + 1, 2), "beta");
             check_cuda(launch_cg_xpay(s, z, pp, sc, N), "xpay");
@@ -1127,7 +1185,11 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
             h[0].u[0] = static_cast<T *>(out);
             h[0].u[1] = tmp.as<T>();
             h[0].aux = tmp.as<T>() + nl;
-            for (int sw = 0; sw < nsweeps; ++sw) push_items(items, 0, p.lev[level].ncol, sw & 1, 1 - (sw & 1), 0);
+            // block red-black SOR: two half-sweeps per sweep, red then black
+            const int launches = p.opts.smoother == 1 ? 2 * nsweeps : nsweeps;
+            for (int sw = 0; sw < launches; ++sw)
+                push_items(items, 0, p.lev[level].ncol, sw & 1, 1 - (sw & 1), 0,
+                           p.opts.smoother == 1 ? 1 + (sw & 1) : 0);
             break;
         }
         case 3:  // restrict residual: a = b, b = u, out = coarse b
@@ -1153,10 +1215,11 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
         case 1: check_cuda(launch_resid<T>(s, L, it, per, 1, nullptr), "residual"); break;
         case 2: {
             const bool rows = sizeof(T) == 4 && rows_eligible(p, level);
-            for (int sw = 0; sw < nsweeps; ++sw)
+            const int launches = p.opts.smoother == 1 ? 2 * nsweeps : nsweeps;
+            for (int sw = 0; sw < launches; ++sw)
                 launch_smoother<T>(p, s, L, it + sw * per, per, rho, p.nz, 0, rows,
                                    p.lev[level].n % 32 == 0);
-            if (nsweeps & 1)
+            if (launches & 1)
                 check_cuda(cudaMemcpyAsync(out, tmp.p, nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                            "copy back");
             break;
@@ -1214,6 +1277,8 @@ void ellsolve_default_opts(ellsolve_opts *o) {
     o->prolong = 0;
     o->inner_cycles = 3;
     o->use_graph = 1;
+    o->smoother = 0;
+    o->precond = 0;
 }
 
 const char *ellsolve_last_error(void) { return t_last_error.c_str(); }
@@ -1246,6 +1311,8 @@ ellsolve_status ellsolve_create(const ellsolve_grid *grid, double omega2, double
     if (!(o.damping > 0 && o.damping <= 2)) throw Error(ELLSOLVE_ERR_ARG, "damping must be in (0, 2]");
     if (o.coarsest_min < 1) o.coarsest_min = 1;
     if (o.prolong != 0 && o.prolong != 1) throw Error(ELLSOLVE_ERR_ARG, "prolong must be 0 or 1");
+    if (o.smoother != 0 && o.smoother != 1) throw Error(ELLSOLVE_ERR_ARG, "smoother must be 0 or 1");
+    if (o.precond != 0 && o.precond != 1) throw Error(ELLSOLVE_ERR_ARG, "precond must be 0 or 1");
     auto h = std::make_unique<ellsolve_s>();
     h->build(*grid, omega2, lambda2, r_levels, o, static_cast<cudaStream_t>(stream));
     *out = h.release();
@@ -1330,6 +1397,13 @@ ellsolve_status ellsolve_solve_batch(ellsolve_t *handles, int count, const void 
         if (!handles[m] || !rhs[m] || !x[m]) throw Error(ELLSOLVE_ERR_ARG, "null member");
         if (handles[m]->opts.precision != 1 || handles[m]->opts.solver != 0)
             throw Error(ELLSOLVE_ERR_ARG, "batch members need precision 1 and solver 0");
+        // the launch sequence is shared: members may differ in grid, parameters,
+        // smoother and damping, not in sweep counts, prolongation or schedule
+        const ellsolve_opts &a = handles[m]->opts, &z = handles[0]->opts;
+        if (a.nu_pre != z.nu_pre || a.nu_post != z.nu_post || a.nu_coarse != z.nu_coarse ||
+            a.prolong != z.prolong || a.inner_cycles != z.inner_cycles)
+            throw Error(ELLSOLVE_ERR_ARG,
+                        "batch members need equal nu_pre, nu_post, nu_coarse, prolong, inner_cycles");
         mem.push_back(handles[m]);
         f.push_back(static_cast<const double *>(rhs[m]));
         xv.push_back(static_cast<double *>(x[m]));
