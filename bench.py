@@ -269,6 +269,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         extras["ensemble"] = run_ensemble(torch, stream)
         extras["serving"] = run_serving(torch, stream, args.serve_requests)
+        extras["smoothers"] = run_smoothers(torch, stream, args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns*V-cycles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -298,6 +299,60 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_smoothers(torch, stream, workload, reps=3):
+    """Block red-black SOR against damped line Jacobi on the benchmark workload
+    (time to the workload's tolerance, V-cycles, time per V-cycle), and CG with
+    block red-black SSOR against block Jacobi on the box 256 x 256 x 64."""
+    from paper_1307_2036_gb300 import ellsolve, inputs
+    kind, n, nz, graded, w2, l2, rhs_kind, rtol = WORKLOADS[workload]
+    r = inputs.radial_levels(nz, graded=graded)
+    with torch.cuda.stream(stream):
+        f = torch.from_numpy(rhs_for(kind, n, nz, rhs_kind)).to("cuda")
+        x = torch.zeros_like(f)
+    stream.synchronize()
+
+    def timed(sv, f, x, rtol, maxit):
+        sv.solve(f, x, rtol=rtol, maxit=maxit)  # warm-up (graph capture)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            st, res = sv.solve(f, x, rtol=rtol, maxit=maxit)
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps, st, res
+
+    out = {"workload": f"{workload}, rtol {rtol:g}, mixed precision", "multigrid": []}
+    for name, sm, nu, rho in (("line Jacobi 2/2, rho 0.8", 0, 2, 0.8),
+                              ("line RB-SOR 1/1, rho 1", 1, 1, 1.0),
+                              ("line RB-SOR 2/2, rho 1", 1, 2, 1.0)):
+        sv = ellsolve.Solver(kind, n, nz, r, w2, l2, precision=1, use_graph=1, smoother=sm,
+                             nu_pre=nu, nu_post=nu, damping=rho, stream=stream.cuda_stream)
+        sv.autotune()
+        ms, st, res = timed(sv, f, x, rtol, 60)
+        out["multigrid"].append({"smoother": name, "ms_to_rtol": ms, "vcycles": res.iterations,
+                                 "ms_per_vcycle": ms / max(1, res.iterations),
+                                 "rel_residual": res.rel_residual, "status": int(st)})
+        sv.close()
+    del f, x
+    torch.cuda.empty_cache()
+    nb, nzb = 256, 64
+    rb = inputs.radial_levels(nzb, graded=True)
+    with torch.cuda.stream(stream):
+        fb = torch.from_numpy(rhs_for(0, nb, nzb, "uniform")).to("cuda")
+        xb = torch.zeros_like(fb)
+    stream.synchronize()
+    out["pcg"] = {"workload": f"box {nb}x{nb}x{nzb} graded, omega2 0.01, lambda 1, rtol 1e-5, FP64"}
+    for name, pc in (("block Jacobi", 0), ("block RB-SSOR", 1)):
+        sv = ellsolve.Solver(0, nb, nzb, rb, 0.01, 1.0, precision=0, solver=1, precond=pc,
+                             stream=stream.cuda_stream)
+        ms, st, res = timed(sv, fb, xb, 1e-5, 1000)
+        out["pcg"][name] = {"ms_to_rtol": ms, "iterations": res.iterations,
+                            "rel_residual": res.rel_residual}
+        sv.close()
+    return out
 
 
 def run_ensemble(torch, stream, members=32, n=128, nz=64, rtol=1e-8, reps=3):

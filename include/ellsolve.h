@@ -111,6 +111,22 @@ void ellsolve_default_opts(ellsolve_opts *o);
 ellsolve_status ellsolve_create(const ellsolve_grid *grid, double omega2, double lambda2,
                                 const double *r_levels, const ellsolve_opts *opts,
                                 void *stream, ellsolve_t *out);
+/* As ellsolve_create, with vertical background profiles (Sec. 2, the operator
+ * D^(z) of Eq. FullSISLEquation): the equation multiplied by the weight p(r)
+ * r^2, p = (pi*)^gamma c_p theta*, with q = 1 / (1 + (alpha dt)^2 (N*)^2) in
+ * the vertical flux.  The tensor-product structure is unchanged; only the
+ * per-level vectors change:
+ *   p_cell : nz host values, (int p r^2 dr) / (int r^2 dr) over layer k, > 0;
+ *            multiplies V_k in the mass and horizontal terms and in b.
+ *   q_face : nz+1 host values, p(r_k) q(r_k) at interface k, > 0 for k =
+ *            1..nz-1 (entries 0 and nz are not read: the Neumann faces).
+ * Either may be NULL (all ones); both NULL is ellsolve_create.  Copied.
+ * Errors as ellsolve_create, and ERR_ARG for a non-positive or non-finite
+ * profile value.  Servers take no profiles. */
+ellsolve_status ellsolve_create_profiles(const ellsolve_grid *grid, double omega2, double lambda2,
+                                         const double *r_levels, const double *p_cell,
+                                         const double *q_face, const ellsolve_opts *opts,
+                                         void *stream, ellsolve_t *out);
 void ellsolve_destroy(ellsolve_t h);
 
 /* Sizes: unknowns on the finest level, and the hierarchy depth. */

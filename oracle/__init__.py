@@ -49,6 +49,7 @@ def _load():
             "og_rb_ssor": (None, [vp, C.c_int, dp, dp, C.c_double]),
             "og_set_smoother": (None, [vp, C.c_int]),
             "og_set_precond": (None, [vp, C.c_int, C.c_double]),
+            "og_set_profiles": (None, [vp, dp, dp]),
             "og_restrict": (None, [vp, C.c_int, dp, dp]),
             "og_prolong_add": (None, [vp, C.c_int, dp, dp, C.c_int]),
             "og_vcycle": (None, [vp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -95,9 +96,12 @@ class Grid:
     horizontal multigrid hierarchy (level 0 finest)."""
 
     def __init__(self, kind, n, nz, r, omega2, lambda2, mapping=0, side=2 * np.pi,
-                 coarsest_min=4, max_levels=0, smoother=0, precond=0, precond_rho=1.0):
+                 coarsest_min=4, max_levels=0, smoother=0, precond=0, precond_rho=1.0,
+                 p_cell=None, q_face=None):
         """smoother: 0 block Jacobi, 1 block red-black SOR (smooth, vcycle,
-        mg_solve); precond: 0 block Jacobi, 1 block red-black SSOR (pcg_solve)."""
+        mg_solve); precond: 0 block Jacobi, 1 block red-black SSOR (pcg_solve);
+        p_cell[nz], q_face[nz+1]: vertical background profiles (V_k and G_k
+        multipliers), None: the model equation."""
         lib = _load()
         r = _f64(r)
         assert r.shape == (nz + 1,)
@@ -106,6 +110,11 @@ class Grid:
         self._h = lib.og_create(kind, n, nz, mapping, side, _dp(r), omega2, lambda2,
                                 coarsest_min, max_levels)
         lib.og_set_smoother(self._h, smoother)
+        if p_cell is not None or q_face is not None:
+            pc = _f64(np.ones(nz) if p_cell is None else p_cell)
+            qf = _f64(np.ones(nz + 1) if q_face is None else q_face)
+            assert pc.shape == (nz,) and qf.shape == (nz + 1,)
+            lib.og_set_profiles(self._h, _dp(pc), _dp(qf))
         lib.og_set_precond(self._h, precond, precond_rho)
         self.P = lib.og_npanel(self._h)
         self.nlevels = lib.og_nlevels(self._h)

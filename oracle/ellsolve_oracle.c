@@ -470,6 +470,20 @@ static void og_half_sweep(const og_grid *g, int lev, const double *b, double *u,
 
 void og_set_smoother(og_grid *g, int kind) { g->smoother = kind; }
 
+/* Vertical background profiles (Sec. 2, Eq. FullSISLEquation and the vertical
+ * operator D^(z) of the Appendix).  Multiplying the equation by the weight
+ * p(r) r^2, p = (pi*)^gamma c_p theta*, keeps it symmetric: the mass and
+ * horizontal terms of layer k take V_k = int p r^2 dr instead of int r^2 dr,
+ * and the vertical flux through r_k takes p q r^2 / (rho_k - rho_{k-1}) with
+ * q = 1 / (1 + (alpha dt)^2 (N*)^2).  The caller gives p_cell[k] = (int p r^2
+ * dr) / (int r^2 dr) over layer k and q_face[k] = p(r_k) q(r_k) at the
+ * interior interfaces k = 1..nz-1; both 1 give the model equation. */
+void og_set_profiles(og_grid *g, const double *p_cell, const double *q_face)
+{
+    for (int k = 0; k < g->nz; ++k) g->V[k] *= p_cell[k];
+    for (int k = 1; k < g->nz; ++k) g->G[k] *= q_face[k];
+}
+
 void og_set_precond(og_grid *g, int kind, double rho)
 {
     g->precond = kind;

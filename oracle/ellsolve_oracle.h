@@ -74,6 +74,9 @@ void og_rb_ssor(const og_grid *g, int lev, const double *r, double *z, double rh
  * 1 block red-black SOR.  Preconditioner of og_pcg_solve: 0 block Jacobi
  * (default), 1 block red-black SSOR with parameter rho. */
 void og_set_smoother(og_grid *g, int kind);
+/* Vertical background profiles: V_k *= p_cell[k] (k < nz), G_k *= q_face[k]
+ * (0 < k < nz).  Call once, before any other use of the grid. */
+void og_set_profiles(og_grid *g, const double *p_cell, const double *q_face);
 void og_set_precond(og_grid *g, int kind, double rho);
 
 /* Intergrid transfers between level lev_f and lev_f + 1. */

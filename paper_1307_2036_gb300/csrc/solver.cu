@@ -188,7 +188,7 @@ size_t geometry_bytes(const ellsolve_grid &g, const ellsolve_opts &o) {
 // Problem set-up
 // ---------------------------------------------------------------------------
 void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *rl,
-                    const ellsolve_opts &o, cudaStream_t s) {
+                    const ellsolve_opts &o, cudaStream_t s, const double *pc, const double *qf) {
     grid = g;
     opts = o;
     stream = s;
@@ -259,15 +259,24 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
     check_cuda(cudaHostAlloc(reinterpret_cast<void **>(&pinned), 64 * sizeof(double),
                              cudaHostAllocDefault),
                "cudaHostAlloc");
-    rebind(w2, l2, rl);
+    rebind(w2, l2, rl, pc, qf);
 }
 
-void Problem::rebind(double w2, double l2, const double *rl) {
+void Problem::rebind(double w2, double l2, const double *rl, const double *pc, const double *qf) {
     omega2 = w2;
     lambda2 = l2;
     r.assign(rl, rl + nz + 1);
     std::vector<double> V, G;
     radial_vectors(r.data(), nz, V, G);
+    // vertical background profiles: V_k = int p r^2 dr, G_k carries p q
+    if (pc) p_cell.assign(pc, pc + nz);
+    else p_cell.clear();
+    if (qf) q_face.assign(qf, qf + nz + 1);
+    else q_face.clear();
+    if (!p_cell.empty())
+        for (int k = 0; k < nz; ++k) V[k] *= p_cell[k];
+    if (!q_face.empty())
+        for (int k = 1; k < nz; ++k) G[k] *= q_face[k];
     std::vector<double> gv(nz + 1);
     for (int k = 0; k <= nz; ++k) gv[k] = w2 * l2 * G[k];
     std::vector<float> V32h(V.begin(), V.end()), g32h(gv.begin(), gv.end());
@@ -1286,6 +1295,14 @@ const char *ellsolve_last_error(void) { return t_last_error.c_str(); }
 ellsolve_status ellsolve_create(const ellsolve_grid *grid, double omega2, double lambda2,
                                 const double *r_levels, const ellsolve_opts *opts, void *stream,
                                 ellsolve_t *out) {
+    return ellsolve_create_profiles(grid, omega2, lambda2, r_levels, nullptr, nullptr, opts,
+                                    stream, out);
+}
+
+ellsolve_status ellsolve_create_profiles(const ellsolve_grid *grid, double omega2, double lambda2,
+                                         const double *r_levels, const double *p_cell,
+                                         const double *q_face, const ellsolve_opts *opts,
+                                         void *stream, ellsolve_t *out) {
     ELLS_GUARD_BEGIN
     if (!grid || !r_levels || !out) throw Error(ELLSOLVE_ERR_ARG, "null argument");
     *out = nullptr;
@@ -1300,6 +1317,14 @@ ellsolve_status ellsolve_create(const ellsolve_grid *grid, double omega2, double
         throw Error(ELLSOLVE_ERR_ARG, "more than 2^31 unknowns per problem");
     for (int k = 0; k < grid->nz; ++k)
         if (!(r_levels[k + 1] > r_levels[k])) throw Error(ELLSOLVE_ERR_ARG, "r_levels not increasing");
+    if (p_cell)
+        for (int k = 0; k < grid->nz; ++k)
+            if (!(p_cell[k] > 0) || !std::isfinite(p_cell[k]))
+                throw Error(ELLSOLVE_ERR_ARG, "p_cell must be positive and finite");
+    if (q_face)
+        for (int k = 1; k < grid->nz; ++k)
+            if (!(q_face[k] > 0) || !std::isfinite(q_face[k]))
+                throw Error(ELLSOLVE_ERR_ARG, "q_face must be positive and finite at 1..nz-1");
     ellsolve_opts o;
     ellsolve_default_opts(&o);
     if (opts) o = *opts;
@@ -1314,7 +1339,7 @@ ellsolve_status ellsolve_create(const ellsolve_grid *grid, double omega2, double
     if (o.smoother != 0 && o.smoother != 1) throw Error(ELLSOLVE_ERR_ARG, "smoother must be 0 or 1");
     if (o.precond != 0 && o.precond != 1) throw Error(ELLSOLVE_ERR_ARG, "precond must be 0 or 1");
     auto h = std::make_unique<ellsolve_s>();
-    h->build(*grid, omega2, lambda2, r_levels, o, static_cast<cudaStream_t>(stream));
+    h->build(*grid, omega2, lambda2, r_levels, o, static_cast<cudaStream_t>(stream), p_cell, q_face);
     *out = h.release();
     return ELLSOLVE_OK;
     ELLS_GUARD_END

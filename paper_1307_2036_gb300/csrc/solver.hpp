@@ -167,9 +167,13 @@ struct Problem {
 
     ~Problem();
     void build(const ellsolve_grid &g, double w2, double l2, const double *r_levels,
-               const ellsolve_opts &o, cudaStream_t s);
-    // new omega^2, lambda^2 and radial levels on the same grid and nz (reuse)
-    void rebind(double w2, double l2, const double *r_levels);
+               const ellsolve_opts &o, cudaStream_t s, const double *p_cell = nullptr,
+               const double *q_face = nullptr);
+    // new omega^2, lambda^2, radial levels and (nullable) vertical profiles on
+    // the same grid and nz (reuse)
+    void rebind(double w2, double l2, const double *r_levels, const double *p_cell = nullptr,
+                const double *q_face = nullptr);
+    std::vector<double> p_cell, q_face;  // vertical background profiles (empty: none)
     Plan &single_plan();
     size_t footprint_bytes() const;
     void prof_mark_begin(cudaStream_t s);

@@ -49,6 +49,9 @@ _SIGS = {
     "ellsolve_default_opts": (None, [C.POINTER(ellsolve_opts)]),
     "ellsolve_create": (_st, [C.POINTER(ellsolve_grid), _d, _d, C.POINTER(C.c_double),
                               C.POINTER(ellsolve_opts), _vp, C.POINTER(_vp)]),
+    "ellsolve_create_profiles": (_st, [C.POINTER(ellsolve_grid), _d, _d, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(ellsolve_opts), _vp, C.POINTER(_vp)]),
     "ellsolve_destroy": (None, [_vp]),
     "ellsolve_size": (C.c_size_t, [_vp]),
     "ellsolve_num_levels": (_i, [_vp]),
@@ -128,7 +131,7 @@ class Solver:
     """One problem: grid, omega^2, lambda^2, radial levels and solver options."""
 
     def __init__(self, kind, n, nz, r_levels, omega2, lambda2, mapping=0, box_side=None,
-                 stream=None, **opts):
+                 stream=None, p_cell=None, q_face=None, **opts):
         import math
         g = ellsolve_grid(kind=kind, n=n, nz=nz,
                           box_side=2 * math.pi if box_side is None else box_side, mapping=mapping)
@@ -136,8 +139,11 @@ class Solver:
         r = (C.c_double * (nz + 1))(*[float(v) for v in r_levels])
         self.stream = _current_stream() if stream is None else stream
         h = C.c_void_p()
-        check(_lib.ellsolve_create(C.byref(g), float(omega2), float(lambda2), r, C.byref(o),
-                                   C.c_void_p(self.stream), C.byref(h)), "ellsolve_create")
+        pc = None if p_cell is None else (C.c_double * nz)(*[float(v) for v in p_cell])
+        qf = None if q_face is None else (C.c_double * (nz + 1))(*[float(v) for v in q_face])
+        check(_lib.ellsolve_create_profiles(C.byref(g), float(omega2), float(lambda2), r, pc, qf,
+                                            C.byref(o), C.c_void_p(self.stream), C.byref(h)),
+              "ellsolve_create")
         self.h = h
         self.kind, self.n, self.nz, self.P = kind, n, nz, 1 if kind == 0 else 6
         self.opts = o
