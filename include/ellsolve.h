@@ -86,7 +86,10 @@ typedef struct {
                        * the cubed sphere, which has no two-colouring, a half-sweep
                        * updates its columns from the iterate before it (0) */
     int precond;      /* PCG: 0 block Jacobi Dtilde^{-1}; 1 block red-black SSOR
-                       * (half-sweeps red, black, black, red from 0, rho = 1) (0) */
+                       * (half-sweeps red, black, black, red from 0, rho = 1); 2 one
+                       * FP64 V-cycle from 0 with the options above (smoother,
+                       * sweeps, damping, prolongation), CG then taking the flexible
+                       * beta <r, z - z_old> / <r_old, z_old> (0) */
 } ellsolve_opts;
 
 typedef struct {

@@ -38,8 +38,10 @@ typedef struct {
 struct og_grid {
     int kind, P, nz, mapping, nlev;
     int smoother;        /* 0 block Jacobi, 1 block red-black SOR */
-    int precond;         /* PCG: 0 block Jacobi, 1 block red-black SSOR */
+    int precond;         /* PCG: 0 block Jacobi, 1 block red-black SSOR, 2 one V-cycle */
     double precond_rho;  /* relaxation parameter of the SSOR preconditioner */
+    int mg_nu_pre, mg_nu_post, mg_nu_coarse, mg_prolong;  /* V-cycle preconditioner */
+    double mg_rho;
     double side, omega2, lambda2;
     double *r, *V, *G;  /* r[nz+1], V[nz], G[nz+1] */
     og_level lev[MAXLEV];
@@ -190,6 +192,9 @@ og_grid *og_create(int kind, int n, int nz, int mapping, double side, const doub
     g->smoother = 0;
     g->precond = 0;
     g->precond_rho = 1.0;
+    g->mg_nu_pre = g->mg_nu_post = g->mg_nu_coarse = 2;
+    g->mg_rho = 0.8;
+    g->mg_prolong = 0;
     g->kind = kind;
     g->P = kind == 0 ? 1 : 6;
     g->nz = nz;
@@ -490,6 +495,16 @@ void og_set_precond(og_grid *g, int kind, double rho)
     g->precond_rho = rho;
 }
 
+void og_set_mg_precond(og_grid *g, int nu_pre, int nu_post, int nu_coarse, double rho,
+                       int prolong_mode)
+{
+    g->mg_nu_pre = nu_pre;
+    g->mg_nu_post = nu_post;
+    g->mg_nu_coarse = nu_coarse;
+    g->mg_rho = rho;
+    g->mg_prolong = prolong_mode;
+}
+
 void og_smooth_rb(const og_grid *g, int lev, const double *b, double *u, int nsweeps, double rho)
 {
     for (int s = 0; s < nsweeps; ++s) {
@@ -513,10 +528,21 @@ void og_rb_ssor(const og_grid *g, int lev, const double *r, double *z, double rh
 }
 
 void og_line_precond(const og_grid *g, int lev, const double *r, double *z);
+/* z = M^{-1} r.  Kind 2 (Sec. 4.3: multigrid as a preconditioner for a
+ * Krylov method) is one V-cycle of A z = r from z = 0 (Algorithm 1). */
+void og_vcycle(const og_grid *g, const double *b, double *u, int nu_pre, int nu_post,
+               int nu_coarse, double rho, double rho_coarse, int prolong_mode);
 static void og_precond(const og_grid *g, const double *r, double *z)
 {
-    if (g->precond == 1) og_rb_ssor(g, 0, r, z, g->precond_rho);
-    else og_line_precond(g, 0, r, z);
+    if (g->precond == 1) {
+        og_rb_ssor(g, 0, r, z, g->precond_rho);
+    } else if (g->precond == 2) {
+        memset(z, 0, g->lev[0].ncol * g->nz * sizeof(double));
+        og_vcycle(g, r, z, g->mg_nu_pre, g->mg_nu_post, g->mg_nu_coarse, g->mg_rho, 1.0,
+                  g->mg_prolong);
+    } else {
+        og_line_precond(g, 0, r, z);
+    }
 }
 
 void og_smooth(const og_grid *g, int lev, const double *b, double *u, int nsweeps, double rho)
@@ -683,8 +709,8 @@ int og_mg_solve(const og_grid *g, const double *b, double *u, double rtol, int m
     return it;
 }
 
-/* Algorithm PCG with M = Dtilde (block Jacobi over vertical columns) or the
- * block red-black SSOR preconditioner (og_set_precond). */
+/* Algorithm PCG with M = Dtilde (block Jacobi over vertical columns), the
+ * block red-black SSOR preconditioner or one V-cycle (og_set_precond). */
 int og_pcg_solve(const og_grid *g, const double *b, double *u, double rtol, int maxit, double *hist)
 {
     long N = g->lev[0].ncol * g->nz;
@@ -711,9 +737,14 @@ int og_pcg_solve(const og_grid *g, const double *b, double *u, double rtol, int 
             double rel = og_norm(r, N) / r0;
             if (hist) hist[K] = rel;
             if (rel < rtol) break;
+            /* the V-cycle preconditioner is not symmetric (bilinear
+             * prolongation against the 2x2 sum), so its beta is the flexible
+             * (Polak-Ribiere) one, <r_K, z_K - z_{K-1}> / <r_{K-1}, z_{K-1}>,
+             * which equals the standard one for a symmetric M */
+            double cross = g->precond == 2 ? og_dot(r, z, N) : 0.0;
             og_precond(g, r, z);
             double kappa = og_dot(r, z, N);
-            double beta = kappa / kappa_old;
+            double beta = (kappa - cross) / kappa_old;
             for (long m = 0; m < N; ++m) p[m] = z[m] + beta * p[m];
             kappa_old = kappa;
         }

@@ -72,12 +72,16 @@ void og_smooth_rb(const og_grid *g, int lev, const double *b, double *u, int nsw
 void og_rb_ssor(const og_grid *g, int lev, const double *r, double *z, double rho);
 /* Smoother of og_smooth / og_vcycle / og_mg_solve: 0 block Jacobi (default),
  * 1 block red-black SOR.  Preconditioner of og_pcg_solve: 0 block Jacobi
- * (default), 1 block red-black SSOR with parameter rho. */
+ * (default), 1 block red-black SSOR with parameter rho, 2 one V-cycle. */
 void og_set_smoother(og_grid *g, int kind);
 /* Vertical background profiles: V_k *= p_cell[k] (k < nz), G_k *= q_face[k]
  * (0 < k < nz).  Call once, before any other use of the grid. */
 void og_set_profiles(og_grid *g, const double *p_cell, const double *q_face);
 void og_set_precond(og_grid *g, int kind, double rho);
+/* Kind 2 of og_set_precond: one V-cycle from zero (the grid's smoother) with
+ * these sweeps, damping and prolongation; PCG then takes the flexible beta. */
+void og_set_mg_precond(og_grid *g, int nu_pre, int nu_post, int nu_coarse, double rho,
+                       int prolong_mode);
 
 /* Intergrid transfers between level lev_f and lev_f + 1. */
 void og_restrict(const og_grid *g, int lev_f, const double *r_f, double *b_c);

@@ -1848,8 +1848,11 @@ __global__ void k_cg_scalars(double *scalars, const double *sums, int op) {
         scalars[kKappa] = sums[0];
     } else if (op == 1) {
         scalars[kAlpha] = scalars[kKappa] / sums[0];
-    } else {
+    } else if (op == 2) {
         scalars[kBeta] = sums[0] / scalars[kKappa];
+        scalars[kKappa] = sums[0];
+    } else {  // flexible beta: (<r, z> - <r, z_old>) / kappa_old
+        scalars[kBeta] = (sums[0] - sums[1]) / scalars[kKappa];
         scalars[kKappa] = sums[0];
     }
 }

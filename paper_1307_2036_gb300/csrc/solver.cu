@@ -1057,6 +1057,13 @@ static ellsolve_status solve_pcg(Problem &p, const double *f, double *x, double 
            *q = p.cg[3].as<double>();
     if (p.cg_scal.bytes == 0) p.cg_scal.alloc(8 * sizeof(double));
     double *sc = p.cg_scal.as<double>();
+    // the V-cycle preconditioner's program and items exist before any item
+    // pointer is taken (building them may move the item buffer)
+    const bool mgpc = p.opts.precond == 2;
+    if (mgpc) {
+        pl.program(true, std::vector<int>(1, 0));
+        pl.sync_items();
+    }
     const Lv<double> *L = pl.desc64.as<Lv<double>>();
     const Item *it = pl.ditems.as<Item>() + pl.norm_off[0];
     const int ni = pl.norm_n;
@@ -1085,7 +1092,17 @@ static ellsolve_status solve_pcg(Problem &p, const double *f, double *x, double 
         upload(sitems, items, s);
     }
     auto precond_dot = [&]() {
-        if (ssor) {
+        if (mgpc) {
+            // one FP64 V-cycle of A z = r from z = 0 on the multigrid hierarchy
+            check_cuda(cudaMemcpyAsync(p.h64[0].b, r, N * 8, cudaMemcpyDeviceToDevice, s), "r");
+            p.fine_cur = 0;
+            vcycle64_once(pl, true);
+            check_cuda(cudaMemcpyAsync(z, p.h64[0].u[p.fine_cur], N * 8, cudaMemcpyDeviceToDevice,
+                                       s),
+                       "z");
+            check_cuda(launch_dot(s, L, it, ni, r, z, part), "dot");
+            p.launches += 1;
+        } else if (ssor) {
             for (int h = 0; h < 4; ++h)
                 launch_smoother<double>(p, s, sdesc.as<Lv<double>>(), sitems.as<Item>() + h * per0,
                                         per0, 1.0, p.nz, h == 0 ? 1 : 0, false, 0);
@@ -1119,9 +1136,16 @@ static ellsolve_status solve_pcg(Problem &p, const double *f, double *x, double 
             rel = read_norms(pl, 1) / r0;
             hist.push_back(rel);
             if (rel < rtol || !std::isfinite(rel)) break;
+            if (mgpc) {
+                // the V-cycle is not a symmetric operator: flexible (Polak-Ribiere)
+                // beta = (<r, z> - <r, z_old>) / kappa_old
+                check_cuda(launch_dot(s, L, it, ni, r, z, part), "dot");
+                check_cuda(launch_finalize(s, part, first, 1, nrm + 2, 0, nullptr, nullptr), "fin");
+                p.launches += 2;
+            }
             precond_dot();
             check_cuda(launch_finalize(s, part, first, 1, nrm + 1, 0, nullptr, nullptr), "fin");
-            check_cuda(launch_cg_scalars(s, sc, nrm + 1, 2), "beta");
+            check_cuda(launch_cg_scalars(s, sc, nrm + 1, mgpc ? 3 : 2), "beta");
             check_cuda(launch_cg_xpay(s, z, pp, sc, N), "xpay");
             p.launches += 4;
         }
@@ -1337,7 +1361,7 @@ ellsolve_status ellsolve_create_profiles(const ellsolve_grid *grid, double omega
     if (o.coarsest_min < 1) o.coarsest_min = 1;
     if (o.prolong != 0 && o.prolong != 1) throw Error(ELLSOLVE_ERR_ARG, "prolong must be 0 or 1");
     if (o.smoother != 0 && o.smoother != 1) throw Error(ELLSOLVE_ERR_ARG, "smoother must be 0 or 1");
-    if (o.precond != 0 && o.precond != 1) throw Error(ELLSOLVE_ERR_ARG, "precond must be 0 or 1");
+    if (o.precond < 0 || o.precond > 2) throw Error(ELLSOLVE_ERR_ARG, "precond must be 0, 1 or 2");
     auto h = std::make_unique<ellsolve_s>();
     h->build(*grid, omega2, lambda2, r_levels, o, static_cast<cudaStream_t>(stream), p_cell, q_face);
     *out = h.release();
