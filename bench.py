@@ -67,7 +67,8 @@ class ClockSampler:
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        out = os.environ.get("ELLSOLVE_CLOCKS_DIR", os.path.join(ROOT, "gpurun_out"))
+        self.path = os.path.join(out, f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:
