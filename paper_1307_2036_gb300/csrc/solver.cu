@@ -795,10 +795,13 @@ static ellsolve_status solve_mg64(Problem &p, const double *f, double *x, double
         }
         if (iters > maxit) iters = maxit;
     }
-    check_cuda(cudaMemcpyAsync(x, bnorm > 0 ? p.h64[0].u[p.fine_cur] : p.h64[0].b, p.N * 8,
-                               cudaMemcpyDeviceToDevice, s),
-               "copy out");
-    if (bnorm == 0) check_cuda(cudaMemsetAsync(x, 0, p.N * 8, s), "zero x");
+    // no V-cycle ran (zero right-hand side or maxit 0): the solution is the zero
+    // start, not whatever the hierarchy holds
+    if (bnorm > 0 && iters > 0)
+        check_cuda(cudaMemcpyAsync(x, p.h64[0].u[p.fine_cur], p.N * 8, cudaMemcpyDeviceToDevice, s),
+                   "copy out");
+    else
+        check_cuda(cudaMemsetAsync(x, 0, p.N * 8, s), "zero x");
     check_cuda(cudaStreamSynchronize(s), "solve sync");
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return finish(rel, iters, rtol, stag, res, secs);

@@ -129,14 +129,16 @@ def test_kernels_fp32(torch_mod, oracle_mod, case):
 
 
 # Levels with n % 32 == 0 (the line smoother's aligned variant: panel-edge
-# neighbours written into its staging ring) and n % 64 == 0 (the row-staged
-# restriction), on the sphere with both mappings and on the periodic box.
+# neighbours written into its staging ring), n % 64 == 0 (the row-staged
+# restriction) and n = 48 (the unaligned variant with a separate neighbour
+# buffer), on the sphere with both mappings and on the periodic box.
 ALIGNED = [
     (1, 64, 16, True, 0, 0.01, 1.0),
     (1, 128, 8, False, 1, 0.05, 4.0),
     (0, 128, 16, True, 0, 0.02, 0.25),
+    (1, 48, 16, True, 0, 0.01, 1.0),     # n % 32 != 0 and above the small-level size
 ]
-AIDS = ["sph64", "sph128e", "box128"]
+AIDS = ["sph64", "sph128e", "box128", "sph48"]
 
 
 @pytest.mark.parametrize("case", ALIGNED, ids=AIDS)
