@@ -51,6 +51,8 @@ def _load():
             "og_set_precond": (None, [vp, C.c_int, C.c_double]),
             "og_set_profiles": (None, [vp, dp, dp]),
             "og_set_mg_precond": (None, [vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]),
+            "og_fmg": (None, [vp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                              C.c_int]),
             "og_restrict": (None, [vp, C.c_int, dp, dp]),
             "og_prolong_add": (None, [vp, C.c_int, dp, dp, C.c_int]),
             "og_vcycle": (None, [vp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -237,6 +239,14 @@ class Grid:
         u = _f64(u).reshape(self.shape()).copy()
         _load().og_vcycle(self._h, _dp(b), _dp(u), nu_pre, nu_post, nu_coarse, rho,
                           rho_coarse, prolong_mode)
+        return u
+
+    def fmg(self, b, nu_pre=2, nu_post=2, nu_coarse=2, rho=0.8, rho_coarse=1.0, prolong_mode=0):
+        """One full-multigrid cycle from zero; returns u."""
+        b = _f64(b).reshape(self.shape())
+        u = np.zeros_like(b)
+        _load().og_fmg(self._h, _dp(b), _dp(u), nu_pre, nu_post, nu_coarse, rho, rho_coarse,
+                       prolong_mode)
         return u
 
     def mg_solve(self, b, rtol=1e-5, maxit=50, nu_pre=2, nu_post=2, nu_coarse=2, rho=0.8,

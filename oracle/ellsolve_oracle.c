@@ -10,6 +10,8 @@
  *   block (line) relaxation   Sec. 4.2, Eq. BlockRBSOR with the Jacobi ordering
  *   Thomas algorithm          Algorithm Thomas (appendix)
  *   V-cycle                   Algorithm 1 (Sec. 4.3), components of Sec. 6.2.1
+ *   full multigrid            Sec. 4.3 (first guess built from the coarsest
+ *                             level upwards, one V-cycle per level)
  *   PCG                       Algorithm PCG (appendix), sign of the residual
  *                             update read as r_K = r_{K-1} - alpha q_{K-1}
  *
@@ -670,6 +672,34 @@ void og_vcycle(const og_grid *g, const double *b, double *u, int nu_pre, int nu_
                int nu_coarse, double rho, double rho_coarse, int prolong_mode)
 {
     og_vcycle_level(g, 0, b, u, nu_pre, nu_post, nu_coarse, rho, rho_coarse, prolong_mode);
+}
+
+/* Full multigrid (Sec. 4.3): the right-hand side restricted to every level
+ * (cell averages in volume-integrated form: sums of the children), nu_coarse
+ * sweeps on the coarsest level from zero, then on each finer level the
+ * coarse solution prolongated as the start of one V-cycle of that level. */
+void og_fmg(const og_grid *g, const double *b, double *u, int nu_pre, int nu_post, int nu_coarse,
+            double rho, double rho_coarse, int prolong_mode)
+{
+    int L = g->nlev;
+    double *bl[MAXLEV], *ul[MAXLEV];
+    for (int l = 0; l < L; ++l) {
+        long N = g->lev[l].ncol * g->nz;
+        bl[l] = l == 0 ? (double *)b : (double *)malloc(N * sizeof(double));
+        ul[l] = l == 0 ? u : (double *)malloc(N * sizeof(double));
+        memset(ul[l], 0, N * sizeof(double));
+    }
+    for (int l = 0; l + 1 < L; ++l) og_restrict(g, l, bl[l], bl[l + 1]);
+    og_smooth(g, L - 1, bl[L - 1], ul[L - 1], nu_coarse, rho_coarse);
+    for (int l = L - 2; l >= 0; --l) {
+        og_prolong_add(g, l, ul[l + 1], ul[l], prolong_mode);  /* onto zero: interpolation */
+        og_vcycle_level(g, l, bl[l], ul[l], nu_pre, nu_post, nu_coarse, rho, rho_coarse,
+                        prolong_mode);
+    }
+    for (int l = 1; l < L; ++l) {
+        free(bl[l]);
+        free(ul[l]);
+    }
 }
 
 static double og_norm(const double *x, long N)

@@ -91,6 +91,12 @@ void og_prolong_add(const og_grid *g, int lev_f, const double *u_c, double *u_f,
 void og_vcycle(const og_grid *g, const double *b, double *u, int nu_pre, int nu_post,
                int nu_coarse, double rho, double rho_coarse, int prolong_mode);
 
+/* Full multigrid: b restricted to every level, the coarsest level smoothed
+ * from zero, then on each finer level the prolongated coarse solution as the
+ * start of one V-cycle.  u (finest level) is overwritten. */
+void og_fmg(const og_grid *g, const double *b, double *u, int nu_pre, int nu_post, int nu_coarse,
+            double rho, double rho_coarse, int prolong_mode);
+
 /* Solvers starting from u = 0.  hist[0..maxit] receives ||r_K||/||r_0||.
  * Return the number of iterations done. */
 int og_mg_solve(const og_grid *g, const double *b, double *u, double rtol, int maxit,
