@@ -90,6 +90,13 @@ typedef struct {
                        * FP64 V-cycle from 0 with the options above (smoother,
                        * sweeps, damping, prolongation), CG then taking the flexible
                        * beta <r, z - z_old> / <r_old, z_old> (0) */
+    int fmg;          /* 1: every V-cycle that starts from a zero iterate (the first
+                       * cycle of precision-0 multigrid, the first inner cycle of each
+                       * refinement step, the precond-2 preconditioner) is one full
+                       * multigrid cycle (Sec. 4.3): the right-hand side restricted to
+                       * every level, nu_coarse sweeps from zero on the coarsest, then
+                       * per finer level the interpolated coarse solution as the start
+                       * of one V-cycle from that level (0) */
 } ellsolve_opts;
 
 typedef struct {

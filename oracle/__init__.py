@@ -51,6 +51,7 @@ def _load():
             "og_set_precond": (None, [vp, C.c_int, C.c_double]),
             "og_set_profiles": (None, [vp, dp, dp]),
             "og_set_mg_precond": (None, [vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]),
+            "og_set_fmg": (None, [vp, C.c_int]),
             "og_fmg": (None, [vp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                               C.c_int]),
             "og_restrict": (None, [vp, C.c_int, dp, dp]),
@@ -100,12 +101,13 @@ class Grid:
 
     def __init__(self, kind, n, nz, r, omega2, lambda2, mapping=0, side=2 * np.pi,
                  coarsest_min=4, max_levels=0, smoother=0, precond=0, precond_rho=1.0,
-                 p_cell=None, q_face=None, mg_precond=None):
+                 p_cell=None, q_face=None, mg_precond=None, fmg=False):
         """smoother: 0 block Jacobi, 1 block red-black SOR (smooth, vcycle,
         mg_solve); precond: 0 block Jacobi, 1 block red-black SSOR, 2 one V-cycle
         (pcg_solve; mg_precond = (nu_pre, nu_post, nu_coarse, rho, prolong));
         p_cell[nz], q_face[nz+1]: vertical background profiles (V_k and G_k
-        multipliers), None: the model equation."""
+        multipliers), None: the model equation; fmg: the first cycle of
+        mg_solve and the V-cycle preconditioner are full multigrid cycles."""
         lib = _load()
         r = _f64(r)
         assert r.shape == (nz + 1,)
@@ -122,6 +124,7 @@ class Grid:
         lib.og_set_precond(self._h, precond, precond_rho)
         if mg_precond is not None:
             lib.og_set_mg_precond(self._h, *mg_precond)
+        lib.og_set_fmg(self._h, 1 if fmg else 0)
         self.P = lib.og_npanel(self._h)
         self.nlevels = lib.og_nlevels(self._h)
 

@@ -43,6 +43,7 @@ struct og_grid {
     int precond;         /* PCG: 0 block Jacobi, 1 block red-black SSOR, 2 one V-cycle */
     double precond_rho;  /* relaxation parameter of the SSOR preconditioner */
     int mg_nu_pre, mg_nu_post, mg_nu_coarse, mg_prolong;  /* V-cycle preconditioner */
+    int fmg;             /* cycles from a zero iterate are full multigrid cycles */
     double mg_rho;
     double side, omega2, lambda2;
     double *r, *V, *G;  /* r[nz+1], V[nz], G[nz+1] */
@@ -507,6 +508,8 @@ void og_set_mg_precond(og_grid *g, int nu_pre, int nu_post, int nu_coarse, doubl
     g->mg_prolong = prolong_mode;
 }
 
+void og_set_fmg(og_grid *g, int on) { g->fmg = on ? 1 : 0; }
+
 void og_smooth_rb(const og_grid *g, int lev, const double *b, double *u, int nsweeps, double rho)
 {
     for (int s = 0; s < nsweeps; ++s) {
@@ -540,8 +543,12 @@ static void og_precond(const og_grid *g, const double *r, double *z)
         og_rb_ssor(g, 0, r, z, g->precond_rho);
     } else if (g->precond == 2) {
         memset(z, 0, g->lev[0].ncol * g->nz * sizeof(double));
-        og_vcycle(g, r, z, g->mg_nu_pre, g->mg_nu_post, g->mg_nu_coarse, g->mg_rho, 1.0,
-                  g->mg_prolong);
+        if (g->fmg)
+            og_fmg(g, r, z, g->mg_nu_pre, g->mg_nu_post, g->mg_nu_coarse, g->mg_rho, 1.0,
+                   g->mg_prolong);
+        else
+            og_vcycle(g, r, z, g->mg_nu_pre, g->mg_nu_post, g->mg_nu_coarse, g->mg_rho, 1.0,
+                      g->mg_prolong);
     } else {
         og_line_precond(g, 0, r, z);
     }
@@ -728,7 +735,10 @@ int og_mg_solve(const og_grid *g, const double *b, double *u, double rtol, int m
     int it = 0;
     if (r0 == 0.0) { free(r); return 0; }
     while (it < maxit) {
-        og_vcycle(g, b, u, nu_pre, nu_post, nu_coarse, rho, rho_coarse, prolong_mode);
+        if (it == 0 && g->fmg)  /* the first cycle starts from zero */
+            og_fmg(g, b, u, nu_pre, nu_post, nu_coarse, rho, rho_coarse, prolong_mode);
+        else
+            og_vcycle(g, b, u, nu_pre, nu_post, nu_coarse, rho, rho_coarse, prolong_mode);
         ++it;
         og_residual(g, 0, b, u, r);
         double rel = og_norm(r, N) / r0;

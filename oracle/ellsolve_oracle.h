@@ -91,6 +91,10 @@ void og_prolong_add(const og_grid *g, int lev_f, const double *u_c, double *u_f,
 void og_vcycle(const og_grid *g, const double *b, double *u, int nu_pre, int nu_post,
                int nu_coarse, double rho, double rho_coarse, int prolong_mode);
 
+/* With on != 0 the first cycle of og_mg_solve and the V-cycle preconditioner
+ * (og_set_precond kind 2) are full multigrid cycles (og_fmg). */
+void og_set_fmg(og_grid *g, int on);
+
 /* Full multigrid: b restricted to every level, the coarsest level smoothed
  * from zero, then on each finer level the prolongated coarse solution as the
  * start of one V-cycle.  u (finest level) is overwritten. */

@@ -1314,6 +1314,45 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// Restriction of the right-hand side alone (full multigrid, Sec. 4.3): the
+// coarse right-hand side is the sum over the 2x2 children (the residual of a
+// zero iterate, restricted as above).  One thread per coarse column; the
+// loads of kPB levels are issued before their sums.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlk) k_restrict_rhs(const Lv<T> *__restrict__ L,
+                                                       const Item *__restrict__ items) {
+    const Item it = items[blockIdx.x];
+    const Lv<T> &d = L[it.lv];
+    const Lv<T> &dc = L[it.lv + 1];
+    const int C = it.col0 + threadIdx.x;
+    const int ncc = dc.ncol;
+    if (C >= ncc) return;
+    const int nz = d.nz, nf = d.n, ncn = dc.n, nc = d.ncol;
+    const int I = C % ncn, t = C / ncn, J = t % ncn, p = t / ncn;
+    const int f0 = (p * nf + 2 * J) * nf + 2 * I;
+    const T *__restrict__ b = d.b;
+    T *__restrict__ bc = dc.b;
+    for (int k0 = 0; k0 < nz; k0 += 8) {
+        T s0[8], s1[8], s2[8], s3[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = k0 + j < nz ? k0 + j : nz - 1;
+            const T *row = b + size_t(k) * nc + f0;
+            s0[j] = __ldg(row);
+            s1[j] = __ldg(row + 1);
+            s2[j] = __ldg(row + nf);
+            s3[j] = __ldg(row + nf + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (k0 + j >= nz) break;
+            bc[size_t(k0 + j) * ncc + C] = (s0[j] + s1[j]) + (s2[j] + s3[j]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Residual fused with the restriction, row-staged (FP32, fine n % 64 == 0).
 // A warp takes 32 coarse columns of one coarse row J: the 2 x 2 children of
 // each lie in fine rows 2J and 2J+1, 64 fine columns wide.  Per level it
@@ -1503,7 +1542,8 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
 // interpolation): cell-centred bilinear weights 9/16, 3/16, 3/16, 1/16; where
 // three cells meet at a cube corner, 1/2, 1/4, 1/4.  The loads of kPB levels
 // are issued before their arithmetic and stores, so each thread keeps 5 kPB
-// loads in flight.
+// loads in flight.  Items flagged zero interpolate onto a zero fine iterate
+// (the start of each level of full multigrid) without reading it.
 // ---------------------------------------------------------------------------
 constexpr int kPB = 8;
 
@@ -1522,6 +1562,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
     const int sw = corner ? s.x : s.w;
     const T *__restrict__ uc = dc.u[it.in];
     T *__restrict__ uf = d.u[it.out];
+    const bool onto_zero = it.zero;  // interpolation only: the fine iterate is zero
     for (int k0 = 0; k0 < nz; k0 += kPB) {
         T cx[kPB], cy[kPB], cz[kPB], cw[kPB], fv[kPB];
 #pragma unroll
@@ -1532,7 +1573,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
             cy[j] = __ldg(row + s.y);
             cz[j] = __ldg(row + s.z);
             cw[j] = __ldg(row + sw);
-            fv[j] = uf[size_t(k) * nc + f];
+            fv[j] = onto_zero ? T(0) : uf[size_t(k) * nc + f];
         }
 #pragma unroll
         for (int j = 0; j < kPB; ++j) {
@@ -2031,6 +2072,13 @@ cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item 
 }
 
 template <typename T>
+cudaError_t launch_restrict_rhs(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems) {
+    if (nitems <= 0) return cudaSuccess;
+    k_restrict_rhs<T><<<nitems, kBlk, 0, s>>>(L, items);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
                                int mode) {
     if (nitems <= 0) return cudaSuccess;
@@ -2154,6 +2202,7 @@ cudaError_t launch_cg_scalars(cudaStream_t s, double *scalars, const double *sum
                                          double *);                                              \
     template cudaError_t launch_restrict_resid<T>(cudaStream_t, const Lv<T> *, const Item *,     \
                                                   int);                                          \
+    template cudaError_t launch_restrict_rhs<T>(cudaStream_t, const Lv<T> *, const Item *, int);  \
     template cudaError_t launch_prolong_add<T>(cudaStream_t, const Lv<T> *, const Item *, int,   \
                                                int);                                             \
     template cudaError_t launch_form_rhs<T>(cudaStream_t, const Lv<T> *, const Item *, int,      \

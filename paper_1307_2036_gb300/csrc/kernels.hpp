@@ -46,8 +46,14 @@ cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int 
 template <typename T>
 cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems);
 
-// u[out] of descriptor lv += P u[in] of descriptor lv+1 (items: fine columns).
-// mode 0 bilinear, 1 constant.
+// b of descriptor lv+1 = 2x2 sums of b on descriptor lv (full multigrid).
+// Items run over the coarse columns.
+template <typename T>
+cudaError_t launch_restrict_rhs(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems);
+
+// u[out] of descriptor lv += P u[in] of descriptor lv+1 (items: fine columns);
+// items flagged zero write P u[in] without reading u[out].  mode 0 bilinear,
+// 1 constant.
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
                                int mode);

@@ -394,8 +394,10 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
 
 // Build the V-cycle program for the plan's members.  fine_zero: the finest
 // iterate is zero on entry.  fine_cur: its buffer per member on entry.
+// With opts.fmg a cycle from a zero finest iterate is one full-multigrid cycle.
 const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
-    std::string key = fine_zero ? "z" : "n";
+    const bool fmg = fine_zero && mem[0]->opts.fmg != 0;
+    std::string key = fmg ? "F" : (fine_zero ? "z" : "n");
     for (int c : fine_cur) key += char('0' + c);
     auto f = programs.find(key);
     if (f != programs.end()) return f->second;
@@ -491,61 +493,114 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
         }
     };
 
-    // down the V: pre-smoothing and restriction, or the coarsest-level sweeps
-    for (int d = 0; d < maxlev; ++d) {
-        std::vector<std::pair<int, int>> pre, coarse;
-        for (int m = 0; m < M; ++m) {
-            if (d < lvl_count(m) - 1) pre.push_back({m, d});
-            else if (d == lvl_count(m) - 1) coarse.push_back({m, d});
-        }
-        const int sweeps = std::max(pre.empty() ? 0 : o.nu_pre, coarse.empty() ? 0 : o.nu_coarse);
-        for (int sw = 0; sw < sweeps; ++sw) {
-            std::vector<std::pair<int, int>> a, b;
-            if (sw < o.nu_pre) a = pre;
-            if (sw < o.nu_coarse) b = coarse;
-            emit_smooth(a, false);
-            emit_smooth(b, true);
-        }
-        if (o.nu_coarse == 0) emit_memsets(coarse);
-        if (!pre.empty()) {
-            emit_memsets(pre);
-            // one launch for the levels the row-staged kernel takes, one for the rest
-            std::vector<std::pair<int, int>> rows_pre, other_pre;
-            for (auto ml : pre)
-                (precision == 1 && restrict_rows_eligible(*mem[ml.first], ml.second) ? rows_pre
-                                                                                     : other_pre)
-                    .push_back(ml);
-            for (int pass = 0; pass < 2; ++pass) {
-                const auto &list = pass == 0 ? rows_pre : other_pre;
-                if (list.empty()) continue;
-                Op op;
-                op.kind = Op::kRestrict;
-                op.rows_ok = pass == 0;
-                op.off = int(items.size());
-                for (auto [m, l] : list) {
-                    push_items(items, base[m] + l, mem[m]->lev[l + 1].ncol, st[m].cur[l], 0, 0);
-                    st[m].zero[l + 1] = 1;  // the coarse iterate starts from zero
-                    st[m].cur[l + 1] = 0;
-                }
-                op.n = int(items.size()) - op.off;
-                prog.ops.push_back(op);
-            }
-        }
-    }
-    // up the V: prolongation, correction and post-smoothing
-    for (int d = maxlev - 2; d >= 0; --d) {
-        std::vector<std::pair<int, int>> up;
-        for (int m = 0; m < M; ++m)
-            if (d < lvl_count(m) - 1) up.push_back({m, d});
-        if (up.empty()) continue;
+    // prolongation onto level l of the listed members; onto_zero: the fine
+    // iterate is zero and is overwritten by the interpolation
+    auto emit_prolong = [&](const std::vector<std::pair<int, int>> &up, bool onto_zero) {
         Op op;
         op.kind = Op::kProlong;
         op.off = int(items.size());
-        for (auto [m, l] : up)
-            push_items(items, base[m] + l, mem[m]->lev[l].ncol, st[m].cur[l + 1], st[m].cur[l], 0);
+        for (auto [m, l] : up) {
+            push_items(items, base[m] + l, mem[m]->lev[l].ncol, st[m].cur[l + 1], st[m].cur[l],
+                       onto_zero ? 1 : 0);
+            st[m].zero[l] = 0;
+        }
         op.n = int(items.size()) - op.off;
         prog.ops.push_back(op);
-        for (int sw = 0; sw < o.nu_post; ++sw) emit_smooth(up, false);
+    };
+    // One V-cycle from level top down to each member's coarsest level and back
+    // (Algorithm 1), for the members flagged in `in`.
+    auto emit_v = [&](int top, const std::vector<char> &in) {
+        // down the V: pre-smoothing and restriction, or the coarsest-level sweeps
+        for (int d = top; d < maxlev; ++d) {
+            std::vector<std::pair<int, int>> pre, coarse;
+            for (int m = 0; m < M; ++m) {
+                if (!in[m]) continue;
+                if (d < lvl_count(m) - 1) pre.push_back({m, d});
+                else if (d == lvl_count(m) - 1) coarse.push_back({m, d});
+            }
+            const int sweeps =
+                std::max(pre.empty() ? 0 : o.nu_pre, coarse.empty() ? 0 : o.nu_coarse);
+            for (int sw = 0; sw < sweeps; ++sw) {
+                std::vector<std::pair<int, int>> a, b;
+                if (sw < o.nu_pre) a = pre;
+                if (sw < o.nu_coarse) b = coarse;
+                emit_smooth(a, false);
+                emit_smooth(b, true);
+            }
+            if (o.nu_coarse == 0) emit_memsets(coarse);
+            if (!pre.empty()) {
+                emit_memsets(pre);
+                // one launch for the levels the row-staged kernel takes, one for the rest
+                std::vector<std::pair<int, int>> rows_pre, other_pre;
+                for (auto ml : pre)
+                    (precision == 1 && restrict_rows_eligible(*mem[ml.first], ml.second)
+                         ? rows_pre
+                         : other_pre)
+                        .push_back(ml);
+                for (int pass = 0; pass < 2; ++pass) {
+                    const auto &list = pass == 0 ? rows_pre : other_pre;
+                    if (list.empty()) continue;
+                    Op op;
+                    op.kind = Op::kRestrict;
+                    op.rows_ok = pass == 0;
+                    op.off = int(items.size());
+                    for (auto [m, l] : list) {
+                        push_items(items, base[m] + l, mem[m]->lev[l + 1].ncol, st[m].cur[l], 0,
+                                   0);
+                        st[m].zero[l + 1] = 1;  // the coarse iterate starts from zero
+                        st[m].cur[l + 1] = 0;
+                    }
+                    op.n = int(items.size()) - op.off;
+                    prog.ops.push_back(op);
+                }
+            }
+        }
+        // up the V: prolongation, correction and post-smoothing
+        for (int d = maxlev - 2; d >= top; --d) {
+            std::vector<std::pair<int, int>> up;
+            for (int m = 0; m < M; ++m)
+                if (in[m] && d < lvl_count(m) - 1) up.push_back({m, d});
+            if (up.empty()) continue;
+            emit_prolong(up, false);
+            for (int sw = 0; sw < o.nu_post; ++sw) emit_smooth(up, false);
+        }
+    };
+
+    if (!fmg) {
+        emit_v(0, std::vector<char>(M, 1));
+    } else {
+        // Full multigrid (Sec. 4.3): the right-hand side restricted to every
+        // level, the coarsest level smoothed from zero, then on each finer
+        // level the interpolated coarse solution as the start of one V-cycle.
+        for (int d = 0; d + 1 < maxlev; ++d) {
+            Op op;
+            op.kind = Op::kRestrictRhs;
+            op.off = int(items.size());
+            for (int m = 0; m < M; ++m) {
+                if (d >= lvl_count(m) - 1) continue;
+                push_items(items, base[m] + d, mem[m]->lev[d + 1].ncol, 0, 0, 0);
+                st[m].zero[d + 1] = 1;
+                st[m].cur[d + 1] = 0;
+            }
+            op.n = int(items.size()) - op.off;
+            if (op.n > 0) prog.ops.push_back(op);
+        }
+        std::vector<std::pair<int, int>> coarse;
+        for (int m = 0; m < M; ++m) coarse.push_back({m, lvl_count(m) - 1});
+        for (int sw = 0; sw < o.nu_coarse; ++sw) emit_smooth(coarse, true);
+        if (o.nu_coarse == 0) emit_memsets(coarse);
+        for (int l = maxlev - 2; l >= 0; --l) {
+            std::vector<char> in(M, 0);
+            std::vector<std::pair<int, int>> up;
+            for (int m = 0; m < M; ++m)
+                if (l < lvl_count(m) - 1) {
+                    in[m] = 1;
+                    up.push_back({m, l});
+                }
+            if (up.empty()) continue;
+            emit_prolong(up, true);
+            emit_v(l, in);
+        }
     }
     prog.fine_cur_out.resize(M);
     for (int m = 0; m < M; ++m) prog.fine_cur_out[m] = st[m].cur[0];
@@ -641,6 +696,10 @@ static void run_program(Plan &pl, const Program &prog) {
                                "restrict_rows");
                 else
                     check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n), "restrict");
+                count(pl);
+                break;
+            case Op::kRestrictRhs:
+                check_cuda(launch_restrict_rhs<T>(s, L, it + op.off, op.n), "restrict_rhs");
                 count(pl);
                 break;
             case Op::kProlong:
@@ -1315,6 +1374,7 @@ void ellsolve_default_opts(ellsolve_opts *o) {
     o->use_graph = 1;
     o->smoother = 0;
     o->precond = 0;
+    o->fmg = 0;
 }
 
 const char *ellsolve_last_error(void) { return t_last_error.c_str(); }
@@ -1365,6 +1425,7 @@ ellsolve_status ellsolve_create_profiles(const ellsolve_grid *grid, double omega
     if (o.prolong != 0 && o.prolong != 1) throw Error(ELLSOLVE_ERR_ARG, "prolong must be 0 or 1");
     if (o.smoother != 0 && o.smoother != 1) throw Error(ELLSOLVE_ERR_ARG, "smoother must be 0 or 1");
     if (o.precond < 0 || o.precond > 2) throw Error(ELLSOLVE_ERR_ARG, "precond must be 0, 1 or 2");
+    if (o.fmg != 0 && o.fmg != 1) throw Error(ELLSOLVE_ERR_ARG, "fmg must be 0 or 1");
     auto h = std::make_unique<ellsolve_s>();
     h->build(*grid, omega2, lambda2, r_levels, o, static_cast<cudaStream_t>(stream), p_cell, q_face);
     *out = h.release();
@@ -1453,9 +1514,9 @@ ellsolve_status ellsolve_solve_batch(ellsolve_t *handles, int count, const void 
         // smoother and damping, not in sweep counts, prolongation or schedule
         const ellsolve_opts &a = handles[m]->opts, &z = handles[0]->opts;
         if (a.nu_pre != z.nu_pre || a.nu_post != z.nu_post || a.nu_coarse != z.nu_coarse ||
-            a.prolong != z.prolong || a.inner_cycles != z.inner_cycles)
+            a.prolong != z.prolong || a.inner_cycles != z.inner_cycles || a.fmg != z.fmg)
             throw Error(ELLSOLVE_ERR_ARG,
-                        "batch members need equal nu_pre, nu_post, nu_coarse, prolong, inner_cycles");
+                        "batch members need equal nu_pre, nu_post, nu_coarse, prolong, inner_cycles, fmg");
         mem.push_back(handles[m]);
         f.push_back(static_cast<const double *>(rhs[m]));
         xv.push_back(static_cast<double *>(x[m]));

@@ -81,7 +81,7 @@ size_t geometry_bytes(const ellsolve_grid &g, const ellsolve_opts &o);
 
 // One launch of a V-cycle program.
 struct Op {
-    enum Kind { kSmooth, kRestrict, kProlong, kMemset } kind = kSmooth;
+    enum Kind { kSmooth, kRestrict, kRestrictRhs, kProlong, kMemset } kind = kSmooth;
     int off = 0, n = 0;       // range in the plan's item array
     double rho = 1.0;         // smoother damping
     int max_nz = 0;           // largest nz among the items

@@ -52,7 +52,8 @@ class Pair:
         self.r = inputs.radial_levels(nz, graded=graded)
         self.og = oracle_mod.Grid(kind, n, nz, self.r, omega2, lambda2, mapping=mapping,
                                   coarsest_min=coarsest_min, max_levels=opts.get("max_levels", 0),
-                                  smoother=opts.get("smoother", 0), precond=opts.get("precond", 0))
+                                  smoother=opts.get("smoother", 0), precond=opts.get("precond", 0),
+                                  fmg=bool(opts.get("fmg", 0)))
         self.sv = ellsolve.Solver(kind, n, nz, self.r, omega2, lambda2, mapping=mapping,
                                   precision=precision, solver=solver, coarsest_min=coarsest_min,
                                   **opts)

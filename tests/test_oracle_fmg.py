@@ -9,6 +9,7 @@ finer level the prolongated coarse solution as the start of one V-cycle.
     smaller residual on the seeded uniform right-hand side.
 """
 import numpy as np
+import pytest
 
 from paper_1307_2036_gb300 import inputs
 from test_oracle_operator import fourier_exact
@@ -61,3 +62,31 @@ def test_fmg_two_levels_composes_the_steps(oracle_mod):
         want = g.vcycle(b, u0, nu_coarse=3, prolong_mode=mode)
         got = g.fmg(b, nu_coarse=3, prolong_mode=mode)
         assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_mg_solve_first_cycle_is_fmg(oracle_mod):
+    """With the flag set, multigrid's first cycle is the full multigrid cycle and
+    the later ones V-cycles from its result."""
+    r = inputs.radial_levels(8, graded=True)
+    g = oracle_mod.Grid(1, 8, 8, r, 0.05, 4.0, fmg=True)
+    b = g.volumes() * inputs.uniform_pm1(g.shape(), member=26)
+    u1 = g.mg_solve(b, rtol=0.0, maxit=1)[0]
+    assert np.array_equal(u1, g.fmg(b))
+    u3 = g.mg_solve(b, rtol=0.0, maxit=3)[0]
+    assert np.array_equal(u3, g.vcycle(b, g.vcycle(b, u1)))
+    # and it converges to the same solution as plain multigrid
+    plain = oracle_mod.Grid(1, 8, 8, r, 0.05, 4.0)
+    ua, ita, _ = g.mg_solve(b, rtol=1e-12, maxit=60)
+    ub, itb, _ = plain.mg_solve(b, rtol=1e-12, maxit=60)
+    assert np.linalg.norm(ua - ub) <= 1e-10 * np.linalg.norm(ub)
+    assert ita <= itb
+
+
+@pytest.mark.parametrize("kind,n", [(0, 8), (1, 8)])
+def test_fmg_preconditioned_cg_equals_dense_lu(oracle_mod, kind, n):
+    g = oracle_mod.Grid(kind, n, 4, inputs.radial_levels(4, graded=True), 0.05, 4.0, precond=2,
+                        mg_precond=(2, 2, 2, 0.8, 0), fmg=True)
+    b = g.volumes() * inputs.uniform_pm1(g.shape(), member=27)
+    u, it, hist = g.pcg_solve(b, rtol=1e-13, maxit=50)
+    exact = np.linalg.solve(g.dense(), b.reshape(-1))
+    assert np.linalg.norm(u.reshape(-1) - exact) <= 1e-10 * np.linalg.norm(exact)
