@@ -340,8 +340,9 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_smoothers(torch, stream, workload, reps=3):
-    """Block red-black SOR against damped line Jacobi on the benchmark workload
-    (time to the workload's tolerance, V-cycles, time per V-cycle), and CG with
+    """Block red-black SOR and full multigrid against damped line Jacobi
+    V-cycles on the benchmark workload (time to the workload's tolerance,
+    V-cycles, time per V-cycle), and CG with
     block red-black SSOR against block Jacobi on the box 256 x 256 x 64."""
     from paper_1307_2036_gb300 import ellsolve, inputs
     kind, n, nz, graded, w2, l2, rhs_kind, rtol = WORKLOADS[workload]
@@ -363,11 +364,13 @@ def run_smoothers(torch, stream, workload, reps=3):
         return e0.elapsed_time(e1) / reps, st, res
 
     out = {"workload": f"{workload}, rtol {rtol:g}, mixed precision", "multigrid": []}
-    for name, sm, nu, rho in (("line Jacobi 2/2, rho 0.8", 0, 2, 0.8),
-                              ("line RB-SOR 1/1, rho 1", 1, 1, 1.0),
-                              ("line RB-SOR 2/2, rho 1", 1, 2, 1.0)):
+    for name, sm, nu, rho, fmg in (("line Jacobi 2/2, rho 0.8", 0, 2, 0.8, 0),
+                                   ("line Jacobi 2/2, rho 0.8, full multigrid", 0, 2, 0.8, 1),
+                                   ("line RB-SOR 1/1, rho 1", 1, 1, 1.0, 0),
+                                   ("line RB-SOR 2/2, rho 1", 1, 2, 1.0, 0)):
         sv = ellsolve.Solver(kind, n, nz, r, w2, l2, precision=1, use_graph=1, smoother=sm,
-                             nu_pre=nu, nu_post=nu, damping=rho, stream=stream.cuda_stream)
+                             nu_pre=nu, nu_post=nu, damping=rho, fmg=fmg,
+                             stream=stream.cuda_stream)
         sv.autotune()
         ms, st, res = timed(sv, f, x, rtol, 60)
         out["multigrid"].append({"smoother": name, "ms_to_rtol": ms, "vcycles": res.iterations,
