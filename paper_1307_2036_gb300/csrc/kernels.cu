@@ -826,6 +826,73 @@ __global__ void __launch_bounds__(kT2) k_smooth_rows2(const Lv<float> *__restric
 }
 
 // ---------------------------------------------------------------------------
+// Tensor memory (TMEM, 128 lanes x 512 32-bit columns per SM) as per-thread
+// scratch.  A CTA of 128 threads allocates a power-of-two number of columns;
+// warp w reaches lanes 32w .. 32w+31, so thread t owns lane t.  The .sync
+// .aligned forms are executed by every thread of the warp.  A tcgen05.ld
+// result may be read only after tcgen05.wait::ld: the wait takes the loaded
+// registers as operands so that no use is scheduled before it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tm_alloc(unsigned *dst_smem, unsigned ncols) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(d),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(unsigned taddr, unsigned ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tm_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tm_st2(unsigned taddr, float2 v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n" ::"r"(taddr),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y))
+                 : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+// 2*FR consecutive columns from taddr into v (FR = 4 or 8)
+template <int FR>
+__device__ __forceinline__ void tm_ld(unsigned taddr, unsigned (&v)[2 * FR]);
+template <>
+__device__ __forceinline__ void tm_ld<4>(unsigned taddr, unsigned (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                   "+r"(v[6]), "+r"(v[7])
+                 :
+                 : "memory");
+}
+template <>
+__device__ __forceinline__ void tm_ld<8>(unsigned taddr, unsigned (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                   "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                   "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+                 :
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Line smoother with twisted elimination, one column per thread.  The
 // tridiagonal system of a column (Algorithm Thomas, excess form) is eliminated
 // from both ends at once: levels 0..m-1 upwards and levels nz-1..m downwards
@@ -860,10 +927,21 @@ __host__ __device__ inline size_t tw_smem_bytes(int max_nz, int fr, bool aln) {
     return size_t(fr) * (kTT / 32) * kSlotF * 4 +          // ring
            (aln ? 0 : size_t(fr) * 4 * kTT * 4) +          // neighbours off the staged rows
            size_t(max_nz / 2 / fr) * kTT * 8 +             // pivot checkpoints
-           size_t(max_nz / 2) * 16;                        // (V_k, V_k') and (g_{k+1}, g_k')
+           size_t(max_nz / 2) * 16 +                       // (V_k, V_k') and (g_{k+1}, g_k')
+           16;                                             // TMEM base address
 }
 
-template <int ZERO, int FR, bool ALN>
+// TM: the parked f' lives in tensor memory instead of the output buffer, one
+// column per elimination step and half (lane = thread).  Columns for a launch
+// whose items have at most max_nz levels (a power of two, 32 .. 512).
+constexpr int kTwTmemMaxNz = 256;
+__host__ __device__ inline int tw_tmem_cols(int max_nz) {
+    int c = 32;
+    while (c < max_nz) c *= 2;
+    return c;
+}
+
+template <int ZERO, int FR, bool ALN, bool TM>
 __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__ L,
                                                    const Item *__restrict__ items, float rho,
                                                    int max_nz) {
@@ -873,6 +951,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     float2 *cpt = reinterpret_cast<float2 *>(fbr + (ALN ? 0 : FR * 4 * kTT));
     float2 *VP = cpt + (max_nz / 2 / FR) * kTT;
     float2 *GH = VP + max_nz / 2;
+    unsigned *tm_sh = reinterpret_cast<unsigned *>(GH + max_nz / 2);
     const Item it = items[blockIdx.x];
     const Lv<float> &d = L[it.lv];
     const int nc = d.ncol, nz = d.nz, n = d.n, m = nz / 2;
@@ -885,11 +964,17 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     // iterate it read instead)
     const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
     constexpr bool zero = ZERO == 1;
+    const unsigned tm_cols = TM ? unsigned(tw_tmem_cols(max_nz)) : 0u;
+    if (TM && warp == 0) tm_alloc(tm_sh, tm_cols);
     for (int i = tid; i < m; i += kTT) {
         VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
         GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
     }
+    if (TM) tm_fence_before();
     __syncthreads();
+    if (TM) tm_fence_after();
+    const unsigned tm0 = TM ? *tm_sh : 0u;
+    const unsigned tm = tm0 + (unsigned(32 * warp) << 16);  // this warp's lanes
     const float *__restrict__ u = d.u[it.in];
     float *__restrict__ un = d.u[it.out];
     const float *__restrict__ b = d.b;
@@ -1077,12 +1162,16 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             const float2 hi = __fmul2_rn(f2(A), hi_g);
             pv = pivot2(__fmul2_rn(Vp, f2(sv)), lo, hi, ratio);
             fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
-            if (active) {
-                *fpb = upd ? fp.x : ucur.x;
-                *fpt = upd ? fp.y : ucur.y;
+            if (TM) {
+                tm_st2(tm + 2u * unsigned(s), fp);
+            } else {
+                if (active) {
+                    *fpb = upd ? fp.x : ucur.x;
+                    *fpt = upd ? fp.y : ucur.y;
+                }
+                fpb += snc;
+                fpt -= snc;
             }
-            fpb += snc;
-            fpt -= snc;
             ratio = pv.ratio_next;
             lo = hi;
             lo_g = hi_g;
@@ -1097,12 +1186,13 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     }
     __threadfence_block();  // the f' stores of this warp are seen by its copies below
     __syncwarp();
+    if (TM) tm_wait_st();
 
     // back substitution, step s = m-1 .. 0; slot fields [0..31] f'_k,
-    // [32..63] g'_k', [64..95] u_k, [96..127] u_k'
+    // [32..63] g'_k', [64..95] u_k, [96..127] u_k' (TM: f' and g' from TMEM)
     const int brow = lane >> 3;
     const int bcol = c0w + 4 * (lane & 7);
-    const bool need = brow < 2 || !zero;
+    const bool need = TM ? (brow >= 2 && !zero) : (brow < 2 || !zero);
     const int nbk = need && bcol + 4 <= nc ? 16 : 0;
     const bool upw = brow & 1;  // the top half runs upwards from m
     const float *pbk = nbk ? (brow < 2 ? (const float *)un : u) + size_t(upw ? m : m - 1) * snc + bcol
@@ -1133,6 +1223,8 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
                 l0 = h1;
             }
         }
+        unsigned fv[2 * FR];  // TM: f' and g' of the block's steps
+        if constexpr (TM) tm_ld<FR>(tm + 2u * unsigned(kb * FR), fv);
         const bool last = kb == 0;
 #pragma unroll
         for (int jj = FR - 1; jj >= 0; --jj) {
@@ -1148,11 +1240,21 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             }
             __syncwarp();
             const float *sk = wring + step * kStride;
-            const float2 fk = make_float2(sk[lane], sk[32 + lane]);
+            float2 fk;
+            if constexpr (TM)
+                fk = make_float2(__uint_as_float(fv[2 * jj]), __uint_as_float(fv[2 * jj + 1]));
+            else
+                fk = make_float2(sk[lane], sk[32 + lane]);
             const float2 uo = zero ? f2(0.f) : make_float2(sk[64 + lane], sk[96 + lane]);
             if (s != m - 1) x = __ffma2_rn(cpr[jj], x, fk);
             const float2 un2 = __ffma2_rn(f2(rho), x, uo);
-            if (active && upd) {
+            if (TM) {
+                // every column is written here, the iterate carried over where !upd
+                if (active) {
+                    __stcs(uob, upd ? un2.x : uo.x);
+                    __stcs(uot, upd ? un2.y : uo.y);
+                }
+            } else if (active && upd) {
                 __stcs(uob, un2.x);
                 __stcs(uot, un2.y);
             }
@@ -1161,6 +1263,11 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
         }
     }
     cp_async_wait<0>();
+    if (TM) {
+        tm_fence_before();
+        __syncthreads();
+        if (warp == 0) tm_dealloc(tm0, tm_cols);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1985,18 +2092,34 @@ cudaError_t launch_smooth_rows2(cudaStream_t s, const Lv<float> *L, const Item *
     return launch_rows2_z<0>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
 
+template <int Z, int FR, bool ALN, bool TM>
+static cudaError_t launch_tw_zfat(cudaStream_t s, const Lv<float> *L, const Item *items,
+                                  int nitems, float rho, int max_nz, int ctas_per_sm) {
+    size_t bytes = tw_smem_bytes(max_nz, FR, ALN);
+    int c = ctas_per_sm;
+    if (TM) {
+        // resident CTAs per SM bounded by TMEM (512 columns): the shared
+        // memory each CTA takes keeps the rest off the SM, so the allocation
+        // in the kernel never waits
+        const int lim = 512 / tw_tmem_cols(max_nz);
+        c = c > 0 ? (c < lim ? c : lim) : lim;
+    }
+    if (c > 0) {
+        const size_t cap = (size_t(228) * 1024) / size_t(c) - 1024;
+        if (cap > bytes) bytes = cap;
+    }
+    cudaError_t e = set_smem(k_smooth_tw<Z, FR, ALN, TM>, bytes);
+    if (e != cudaSuccess) return e;
+    k_smooth_tw<Z, FR, ALN, TM><<<nitems, kTT, bytes, s>>>(L, items, rho, max_nz);
+    return cudaGetLastError();
+}
+
 template <int Z, int FR, bool ALN>
 static cudaError_t launch_tw_zfa(cudaStream_t s, const Lv<float> *L, const Item *items,
                                  int nitems, float rho, int max_nz, int ctas_per_sm) {
-    size_t bytes = tw_smem_bytes(max_nz, FR, ALN);
-    if (ctas_per_sm > 0) {
-        const size_t cap = (size_t(228) * 1024) / size_t(ctas_per_sm) - 1024;
-        if (cap > bytes) bytes = cap;
-    }
-    cudaError_t e = set_smem(k_smooth_tw<Z, FR, ALN>, bytes);
-    if (e != cudaSuccess) return e;
-    k_smooth_tw<Z, FR, ALN><<<nitems, kTT, bytes, s>>>(L, items, rho, max_nz);
-    return cudaGetLastError();
+    if (max_nz <= kTwTmemMaxNz)
+        return launch_tw_zfat<Z, FR, ALN, true>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
+    return launch_tw_zfat<Z, FR, ALN, false>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
 
 template <int Z, int FR>
