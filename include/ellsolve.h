@@ -97,6 +97,13 @@ typedef struct {
                        * every level, nu_coarse sweeps from zero on the coarsest, then
                        * per finer level the interpolated coarse solution as the start
                        * of one V-cycle from that level (0) */
+    int refine;       /* precision 1, the FP64 residual b - A x of each refinement
+                       * step: 0 tracked -- the step updates the stored residual by
+                       * -A e in double-float (pairs of binary32) together with x,
+                       * with a running bound on its rounding; when the bound is not
+                       * below 0.1% of the residual, the residual is recomputed in
+                       * FP64 and later steps recompute it; 1 recomputed in FP64 at
+                       * every step (0) */
 } ellsolve_opts;
 
 typedef struct {

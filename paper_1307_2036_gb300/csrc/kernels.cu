@@ -1695,6 +1695,50 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two
+// binary32 numbers) from the error-free transformations: TwoSum (Knuth),
+// Fast2Sum (Dekker) and the product by one FMA.  The _rn intrinsics keep the
+// compiler from contracting or reassociating them.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// coefficient (double-float) times a binary32 value: c.hi v exactly as two
+// floats, c.lo v added with one rounding
+__device__ __forceinline__ ff mul_ff_f(ff c, float v) {
+    const float p = __fmul_rn(c.hi, v);
+    return {p, __fmaf_rn(c.lo, v, __fmaf_rn(c.hi, v, -p))};
+}
+__device__ __forceinline__ ff mul_ff(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+// a + b, renormalised by TwoSum (the sum may cancel to below either lo)
+__device__ __forceinline__ ff add_ff(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff neg_ff(ff a) { return {-a.hi, -a.lo}; }
+// binary64 -> double-float: hi = RN(d), lo = RN(d - hi) (one FP64 subtraction)
+__device__ __forceinline__ ff split_ff(double d) {
+    const float h = f64_to_f32_rn(d);
+    return {h, f64_to_f32_rn(d - f32_to_f64_pow2(h, 0))};
+}
+
+// ---------------------------------------------------------------------------
 // FP64 outer residual of the iterative refinement.
 // ---------------------------------------------------------------------------
 // MODE 0: general x; 1: x = 0 (r = A V f); 2: x = 0, norm only (r32 untouched)
@@ -1703,29 +1747,54 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                                                       const Lv<float> *__restrict__ L32,
                                                       const Item *__restrict__ items,
                                                       const double *__restrict__ scale,
-                                                      double *__restrict__ partials) {
+                                                      const int *__restrict__ sel, int want,
+                                                      double *__restrict__ partials,
+                                                      double *__restrict__ partials2) {
     const Item it = items[blockIdx.x];
+    if (sel && sel[it.lv] != want) return;  // the whole block: one member
     const Lv<double> &d = L64[it.lv];
     const int c = it.col0 + threadIdx.x;
     const int nc = d.ncol;
-    double acc = 0.0;
+    double acc = 0.0, acc2 = 0.0;
     if (c < nc) {
         const int nz = d.nz;
         const double *__restrict__ x = d.u[0];
         const double *__restrict__ f = d.b;
         const double *__restrict__ V = d.V;
         const double *__restrict__ g = d.g;
-        float *__restrict__ r32 = L32[it.lv].b;
+        const Lv<float> &e32 = L32[it.lv];
+        float *__restrict__ r32 = e32.b;
+        float2 *__restrict__ rt = reinterpret_cast<float2 *>(d.aux);  // scaled residual
         const float sc = float(scale[it.lv]);  // a power of two: exact in FP32
         const Column<double> col = load_column(d, c);
         float colsum = 0.f;  // this column's sum of r^2 (only steers the stopping test)
-        if (MODE != 0) {
-            // x = 0: r = b = A_P V_k f, needed only in FP32 (the inner
-            // right-hand side and its norm), formed in FP32 from the FP32
-            // copies of A_P and V_k
-            const Lv<float> &e32 = L32[it.lv];
+        if (MODE == 1) {
+            // x = 0: r = b = A_P V_k f in double-float (f split into hi + lo
+            // with one FP64 subtraction); r32 = its high part, scaled
+            const ff A = split_ff(col.A);
+            constexpr int B = 8;  // eight levels' loads are issued before their arithmetic
+            for (int k0 = 0; k0 < nz; k0 += B) {
+                double fv[B];
+#pragma unroll
+                for (int j = 0; j < B; ++j) fv[j] = __ldg(f + size_t(min(k0 + j, nz - 1)) * nc + c);
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    const int k = k0 + j;
+                    if (k < nz) {
+                        const ff AV = mul_ff(A, split_ff(__ldg(V + k)));
+                        const ff bk = mul_ff(AV, split_ff(fv[j]));
+                        const size_t o = size_t(k) * nc + c;
+                        const float h = __fmul_rn(bk.hi, sc);
+                        rt[o] = make_float2(h, __fmul_rn(bk.lo, sc));
+                        r32[o] = h;
+                        colsum = __fmaf_rn(bk.hi, bk.hi, colsum);
+                    }
+                }
+            }
+        } else if (MODE == 2) {
+            // x = 0, the norm of b only (fixes the scale), in FP32
             const float A32 = e32.area[c];
-            constexpr int B = 8;  // eight levels' loads are issued before their conversions
+            constexpr int B = 8;
             for (int k0 = 0; k0 < nz; k0 += B) {
                 double fv[B];
 #pragma unroll
@@ -1736,19 +1805,24 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                     if (k < nz) {
                         const float rf =
                             __fmul_rn(__fmul_rn(A32, __ldg(e32.V + k)), f64_to_f32_rn(fv[j]));
-                        if (MODE == 1) r32[size_t(k) * nc + c] = rf * sc;
                         colsum = fmaf(rf, rf, colsum);
                     }
                 }
             }
         } else {
-            // FP64 is the scarce unit here (about 11 FP64 instructions per
+            // FP64 is the scarce unit here (about 12 FP64 instructions per
             // unknown).  The mass and horizontal terms are formed as
             // V_k (s u - sum_q t_q u_q), s = A + sum_q t_q (rounding ~eps C_horiz
             // relative to the mass term, far below the FP64 attainable
             // residual); the vertical term as the difference of the face fluxes
             // G_{k+1} (u_k - u_{k+1}), carried from one level to the next
             // (G_0 = G_nz = 0).   r = A (V_k f - vert) - V_k hm
+            // Also: the scaled residual as double-float, and the magnitude
+            // |u_k| (V_k (s + sum_q t_q) + 2 A (g_k + g_{k+1})) ~ (|A| |x|)_k
+            // whose norm bounds the rounding of this evaluation.
+            const float wsum = f64_to_f32_rn(col.s + ((col.t0 + col.t1) + (col.t2 + col.t3)));
+            const float A32 = e32.area[c];
+            float magsum = 0.f;
             double u0 = __ldg(x + c), flux_lo = 0.0;
 #pragma unroll 2
             for (int k = 0; k < nz; ++k) {
@@ -1765,25 +1839,146 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                 const double vert = flux_hi - flux_lo;
                 const double r = fma(-Vk, hm, col.A * fma(Vk, __ldg(f + o + c), -vert));
                 const float rf = f64_to_f32_rn(r);
-                r32[o + c] = rf * sc;
+                const float rl = f64_to_f32_rn(r - f32_to_f64_pow2(rf, 0));
+                const float h = rf * sc;
+                r32[o + c] = h;
+                rt[o + c] = make_float2(h, rl * sc);
                 colsum = fmaf(rf, rf, colsum);
+                const float mag = fabsf(f64_to_f32_rn(u0)) *
+                                  fmaf(__ldg(e32.V + k), wsum,
+                                       2.f * A32 * (__ldg(e32.g + k) + __ldg(e32.g + k + 1)));
+                magsum = fmaf(mag, mag, magsum);
                 flux_lo = flux_hi;
                 u0 = up;
             }
+            acc2 = double(magsum);
         }
         acc = double(colsum);
     }
     const double t = block_sum(acc);
+    if (MODE == 0) {
+        __syncthreads();  // block_sum's shared slots are reused
+        const double t2 = block_sum(acc2);
+        if (threadIdx.x == 0 && partials2) partials2[blockIdx.x] = t2;
+    }
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Tracked refinement step (members with sel == 1).  With x the FP64 iterate,
+// e the inner correction (FP32, scaled by s = 2^-k) and rt = r s the stored
+// scaled residual (double-float):
+//     x  += e / s                       (one FP64 add)
+//     rt  = (rt - A e) * (s_next / s)   (double-float; A e from the FP64
+//                                        coefficients split into hi + lo)
+//     r32 = hi(rt)                      (the next inner right-hand side)
+// so that the FP64 residual b - A x need not be recomputed.  Each column also
+// adds up ||rt - A e||^2 / s^2 (the new residual norm) and the squared
+// magnitude sum_k (|A| |e| / s)^2 that bounds the rounding of A e; the host
+// keeps the bound and recomputes the residual in FP64 when the tracked value
+// is no longer accurate to 0.1%.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict__ L64,
+                                                   const Lv<float> *__restrict__ L32,
+                                                   const Item *__restrict__ items,
+                                                   const double *__restrict__ scale,
+                                                   const int *__restrict__ sel, int nmembers,
+                                                   int max_nz, double *__restrict__ partials,
+                                                   double *__restrict__ partials2) {
+    extern __shared__ float2 vg_sh[];  // (V_k hi, lo) [max_nz], (g_k hi, lo) [max_nz + 1]
+    float2 *Vh = vg_sh, *gh = vg_sh + max_nz;
+    const Item it = items[blockIdx.x];
+    if (sel[it.lv] != 1) return;
+    const Lv<double> &d = L64[it.lv];
+    const int nz = d.nz, nc = d.ncol;
+    for (int k = threadIdx.x; k <= nz; k += kBlk) {
+        if (k < nz) {
+            const ff v = split_ff(d.V[k]);
+            Vh[k] = make_float2(v.hi, v.lo);
+        }
+        const ff g = split_ff(d.g[k]);
+        gh[k] = make_float2(g.hi, g.lo);
+    }
+    __syncthreads();
+    const int c = it.col0 + threadIdx.x;
+    double acc = 0.0, acc2 = 0.0;
+    const double sc = scale[it.lv], sn = scale[nmembers + it.lv];
+    if (c < nc) {
+        double *__restrict__ x = d.u[0];
+        float2 *__restrict__ rt = reinterpret_cast<float2 *>(d.aux);
+        const Lv<float> &f32 = L32[it.lv];
+        const float *__restrict__ e = f32.u[it.in];
+        float *__restrict__ r32 = f32.b;
+        const long long sb = __double_as_longlong(sc);
+        const int kx = 1023 - static_cast<int>((sb >> 52) & 0x7ff);  // sc = 2^-kx
+        const float ratio = float(sn / sc);                           // a power of two
+        const Column<double> col = load_column(d, c);
+        const ff A = split_ff(col.A), S = split_ff(col.s);
+        const ff T0 = split_ff(col.t0), T1 = split_ff(col.t1), T2 = split_ff(col.t2),
+                 T3 = split_ff(col.t3);
+        float colsum = 0.f, magsum = 0.f;
+        float e0 = __ldg(e + c);
+        ff flux_lo = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = 0; k < nz; ++k) {
+            const size_t o = size_t(k) * nc;
+            const float ep = k + 1 < nz ? __ldg(e + o + nc + c) : 0.f;
+            const float *row = e + o;
+            // s e - sum_q t_q e_q: the hi parts summed by TwoSum, every error
+            // and lo part collected in one float
+            const ff p0 = mul_ff_f(S, e0);
+            const ff p1 = mul_ff_f(neg_ff(T0), __ldg(row + col.nb.x));
+            const ff p2 = mul_ff_f(neg_ff(T1), __ldg(row + col.nb.y));
+            const ff p3 = mul_ff_f(neg_ff(T2), __ldg(row + col.nb.z));
+            const ff p4 = mul_ff_f(neg_ff(T3), __ldg(row + col.nb.w));
+            ff h = two_sum(p0.hi, p1.hi);
+            float err = __fadd_rn(__fadd_rn(p0.lo, p1.lo), h.lo);
+            ff t = two_sum(h.hi, p2.hi);
+            err = __fadd_rn(err, __fadd_rn(p2.lo, t.lo));
+            t = two_sum(t.hi, p3.hi);
+            err = __fadd_rn(err, __fadd_rn(p3.lo, t.lo));
+            t = two_sum(t.hi, p4.hi);
+            err = __fadd_rn(err, __fadd_rn(p4.lo, t.lo));
+            const ff hm = two_sum(t.hi, err);
+            const float2 v2 = Vh[k], g2 = gh[k + 1];
+            const ff Vk = {v2.x, v2.y}, gk1 = {g2.x, g2.y};
+            // vertical: face flux g_{k+1} (e_k - e_{k+1}), carried to the next level
+            const ff flux_hi = mul_ff(gk1, two_sum(e0, -ep));
+            const ff Ae = add_ff(mul_ff(Vk, hm), mul_ff(A, add_ff(flux_hi, neg_ff(flux_lo))));
+            const float2 r2 = rt[o + c];
+            const ff rn = add_ff({r2.x, r2.y}, neg_ff(Ae));
+            const float nh = __fmul_rn(rn.hi, ratio), nl = __fmul_rn(rn.lo, ratio);
+            rt[o + c] = make_float2(nh, nl);
+            r32[o + c] = nh;
+            colsum = __fmaf_rn(rn.hi, rn.hi, colsum);
+            const float mag = __fmaf_rn(
+                v2.x, (fabsf(p0.hi) + fabsf(p1.hi)) + (fabsf(p2.hi) + (fabsf(p3.hi) + fabsf(p4.hi))),
+                A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
+            magsum = __fmaf_rn(mag, mag, magsum);
+            x[o + c] += f32_to_f64_pow2(e0, kx);
+            flux_lo = flux_hi;
+            e0 = ep;
+        }
+        acc = double(colsum);
+        acc2 = double(magsum);
+    }
+    const double inv2 = 1.0 / (sc * sc);
+    const double t1 = block_sum(acc);
+    __syncthreads();  // block_sum's shared slots are reused
+    const double t2 = block_sum(acc2);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = t1 * inv2;
+        partials2[blockIdx.x] = t2 * inv2;
+    }
 }
 
 __global__ void __launch_bounds__(kBlk) k_ir_update(const Lv<double> *__restrict__ L64,
                                                     const Lv<float> *__restrict__ L32,
                                                     const Item *__restrict__ items,
                                                     const double *__restrict__ scale,
-                                                    const int *__restrict__ active) {
+                                                    const int *__restrict__ sel, int want) {
     const Item it = items[blockIdx.x];
-    if (!active[it.lv]) return;
+    if (sel[it.lv] != want) return;
     const Lv<double> &d = L64[it.lv];
     const int c = it.col0 + threadIdx.x;
     const int nc = d.ncol;
@@ -2248,19 +2443,38 @@ cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned 
 
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
-                               double *partials, int x_is_zero) {
+                               double *partials, int x_is_zero, const int *sel, int want,
+                               double *partials2) {
     if (nitems <= 0) return cudaSuccess;
-    if (x_is_zero == 2) k_ir_residual<2><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
-    else if (x_is_zero) k_ir_residual<1><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
-    else k_ir_residual<0><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, partials);
+    if (x_is_zero == 2)
+        k_ir_residual<2><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
+                                                 partials2);
+    else if (x_is_zero)
+        k_ir_residual<1><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
+                                                 partials2);
+    else
+        k_ir_residual<0><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
+                                                 partials2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,
-                             const int *active) {
+                             const int *sel, int want) {
     if (nitems <= 0) return cudaSuccess;
-    k_ir_update<<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, active);
+    k_ir_update<<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_track(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
+                            const Item *items, int nitems, const double *scale, const int *sel,
+                            int nmembers, int max_nz, double *partials, double *partials2) {
+    if (nitems <= 0) return cudaSuccess;
+    const size_t bytes = size_t(2 * max_nz + 1) * sizeof(float2);
+    cudaError_t e = set_smem(k_ir_track, bytes);
+    if (e != cudaSuccess) return e;
+    k_ir_track<<<nitems, kBlk, bytes, s>>>(L64, L32, items, scale, sel, nmembers, max_nz,
+                                           partials, partials2);
     return cudaGetLastError();
 }
 

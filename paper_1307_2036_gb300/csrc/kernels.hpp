@@ -60,9 +60,12 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 
 // Iterative-refinement outer step, per member m (items' lv = member index):
 //   r = A_P V_k f - A x   in FP64, f = L64[m].b (pointwise), x = L64[m].u[0],
-//   L32[m].b = float(r * scale[m]), partials[item] = sum of r^2.
-// x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve);
-// 2 the same but only the norm (r32 is not written).
+//   L32[m].b = float(r * scale[m]), L64[m].aux (float2 pairs) = r * scale[m]
+//   as double-float, partials[item] = sum of r^2, partials2[item] = squared
+//   magnitude of |A| |x| (bound on the rounding of the evaluation).
+// x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve;
+// r and its norm only); 2 the same but only the norm (nothing written).
+// sel: when not null, only members with sel[m] == want take part.
 // Row-staged FP32 residual + restriction; every fine level of the launch has
 // n % 64 == 0.
 cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item *items,
@@ -70,11 +73,20 @@ cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item 
 cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned long long *bad);
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
-                               double *partials, int x_is_zero);
-// x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with active[m] != 0
+                               double *partials, int x_is_zero, const int *sel, int want,
+                               double *partials2);
+// x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with sel[m] == want
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,
-                             const int *active);
+                             const int *sel, int want);
+// Tracked refinement step for members with sel[m] == 1 (scale[m] = s,
+// scale[nmembers + m] = s_next, e = L32[m].u[item.in], rt = L64[m].aux):
+//   x += e / s;  rt = (rt - A e) s_next / s (double-float);  L32[m].b = hi(rt);
+//   partials[item] = sum of (rt - A e)^2 / s^2, partials2[item] = sum of the
+//   squared magnitudes (|A| |e|)^2 / s^2.
+cudaError_t launch_ir_track(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
+                            const Item *items, int nitems, const double *scale, const int *sel,
+                            int nmembers, int max_nz, double *partials, double *partials2);
 
 // b = A_P V_k f on every item (FP64 or FP32 output), partial sums of b^2.
 template <typename T>

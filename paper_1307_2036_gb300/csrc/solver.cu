@@ -170,6 +170,7 @@ size_t problem_vector_bytes(const ellsolve_grid &g, const ellsolve_opts &o) {
         else {
             t += 3 * nl * 4;
             if (smooth_uses_global_scratch(g.nz, 4)) t += nl * 4;
+            if (first) t += nl * 8;  // tracked refinement residual (double-float)
         }
         (void)n;
         (void)first;
@@ -222,6 +223,8 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
             L.u32[1].alloc(nl * 4);
             L.b32.alloc(nl * 4);
             if (glob32) L.aux32.alloc(nl * 4);
+            // finest level: the scaled refinement residual as double-float pairs
+            if (l == 0) L.aux64.alloc(nl * 8);
         }
         Lv<double> &d = h64[l];
         std::memset(&d, 0, sizeof(d));
@@ -324,7 +327,10 @@ void push_items(std::vector<Item> &v, int lv, int ncol, int in, int out, int zer
 
 }  // namespace
 
-Plan::~Plan() { drop_graph(); }
+Plan::~Plan() {
+    drop_graph();
+    if (hnorms) cudaFreeHost(hnorms);
+}
 
 void Plan::drop_graph() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -376,6 +382,7 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
     std::vector<int> first_dev(outer_first.begin(), outer_first.end());
     upload(dfirst, first_dev, s);
     partials.alloc(size_t(std::max(outer_n, 1)) * sizeof(double));
+    partials2.alloc(size_t(std::max(outer_n, 1)) * sizeof(double));
     norms.alloc(size_t(M) * 4 * sizeof(double));
     scales.alloc(size_t(2) * M * sizeof(double));
     std::vector<double> cnt(M), ones(M, 1.0);
@@ -388,7 +395,15 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
                                cudaMemcpyHostToDevice, s),
                "scales");
     check_cuda(cudaStreamSynchronize(s), "plan sync");
-    host_norms.assign(M, 0.0);
+    host_norms.assign(2 * M, 0.0);
+    if (hnorms_n < size_t(4 * M)) {
+        if (hnorms) cudaFreeHost(hnorms);
+        hnorms = nullptr;
+        check_cuda(cudaHostAlloc(reinterpret_cast<void **>(&hnorms), size_t(4 * M) * sizeof(double),
+                                 cudaHostAllocDefault),
+                   "pinned norms");
+        hnorms_n = size_t(4 * M);
+    }
     items_dirty = true;
 }
 
@@ -767,9 +782,11 @@ void Problem::prof_collect(bool graph_replayed) {
 // ---------------------------------------------------------------------------
 // Solvers
 // ---------------------------------------------------------------------------
-static double read_norms(Plan &pl, int M) {
+// the first `count` (<= 2 M) device norms into host_norms
+static double read_norms(Plan &pl, int count) {
+    const int M = count;
     cudaStream_t s = pl.mem[0]->stream;
-    double *h = pl.mem[0]->pinned;
+    double *h = pl.hnorms;
     check_cuda(cudaMemcpyAsync(h, pl.norms.p, M * sizeof(double), cudaMemcpyDeviceToHost, s),
                "norm copy");
     check_cuda(cudaStreamSynchronize(s), "norm sync");
@@ -910,7 +927,7 @@ static void ir_push_state(Plan &pl, const std::vector<MemberRun *> &run) {
     for (int m = 0; m < M; ++m) {
         pl.stage_scales[m] = run[m]->scale_cur;
         pl.stage_scales[M + m] = run[m]->scale_next;
-        pl.stage_active[m] = run[m]->active ? 1 : 0;
+        pl.stage_active[m] = run[m]->active ? run[m]->mode : 0;  // 0 idle, 1 tracked, 2 FP64
     }
     cudaStream_t s = pl.mem[0]->stream;
     check_cuda(cudaMemcpyAsync(pl.scales.p, pl.stage_scales.data(), 2 * M * sizeof(double),
@@ -921,7 +938,8 @@ static void ir_push_state(Plan &pl, const std::vector<MemberRun *> &run) {
                "active");
 }
 
-// FP64 residual of members [m0, m1) formed with scale_next, and its norm
+// FP64 residual of members [m0, m1) formed with scale_next, its norm (norms[m])
+// and, for a general x, the magnitude || |A| |x| || (norms[M + m])
 static void ir_residual_norm(Plan &pl, int m0, int m1, int x_is_zero) {
     cudaStream_t s = pl.mem[0]->stream;
     const int M = int(pl.mem.size());
@@ -929,13 +947,26 @@ static void ir_residual_norm(Plan &pl, int m0, int m1, int x_is_zero) {
     check_cuda(launch_ir_residual(s, pl.outer64.as<Lv<double>>(), pl.fine32.as<Lv<float>>(),
                                   pl.ditems.as<Item>() + pl.outer_off + i0, i1 - i0,
                                   pl.scales.as<double>() + M, pl.partials.as<double>() + i0,
-                                  x_is_zero),
+                                  x_is_zero, nullptr, 0, pl.partials2.as<double>() + i0),
                "ir_residual");
     check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>() + m0, m1 - m0,
                                pl.norms.as<double>() + m0, 1, nullptr, nullptr),
                "finalize");
     count(pl, 2);
+    if (x_is_zero == 0) {
+        check_cuda(launch_finalize(s, pl.partials2.as<double>(), pl.dfirst.as<int>() + m0,
+                                   m1 - m0, pl.norms.as<double>() + M + m0, 1, nullptr, nullptr),
+                   "finalize");
+        count(pl);
+    }
 }
+
+// Rounding bounds of the refinement residual (2-norms, relative to the
+// magnitudes || |A| |v| ||): an FP64 evaluation, and one double-float update
+// (products and sums with binary32 halves, about 12 roundings of 2^-48 each).
+constexpr double kErrFp64 = 0x1p-50;
+constexpr double kErrTrack = 0x1p-44;
+constexpr double kErrRound = 0x1p-52;  // the FP64 rounding of each update of x
 
 // Start members [m0, m1): x = 0 unless keep_x, ||r||, scales, first residual.
 void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep_x) {
@@ -962,6 +993,15 @@ void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep
     }
     ir_push_state(pl, run);
     ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
+    if (keep_x) read_norms(pl, 2 * int(pl.mem.size()));
+    const int M = int(pl.mem.size());
+    for (int m = m0; m < m1; ++m) {
+        MemberRun &r = *run[m];
+        // the stored residual: b in double-float (x = 0), or an FP64 evaluation
+        r.mode = pl.mem[m]->opts.refine == 1 ? 2 : 1;
+        r.magx = keep_x ? pl.host_norms[M + m] : 0.0;
+        r.errb = keep_x ? kErrFp64 * r.magx : 0x1p-45 * r.bnorm;
+    }
 }
 
 // one refinement step: inner V-cycles on r32, x += e / scale_cur, new residual
@@ -978,13 +1018,31 @@ static void ir_step(Plan &pl) {
     }
     pl.sync_items();
     for (const Program *pr : progs) run_program<float>(pl, *pr);
-    check_cuda(launch_ir_update(s, pl.outer64.as<Lv<double>>(), pl.fine32.as<Lv<float>>(),
-                                pl.ditems.as<Item>() + progs.back()->update_off,
-                                progs.back()->update_n, pl.scales.as<double>(),
-                                pl.active.as<int>()),
+    // The end of the step, per member by its mode: FP64 members update x and
+    // recompute the residual; tracked members do both in one double-float
+    // pass.  The update items run over each member's finest columns in member
+    // order, as the outer items do, so the partial sums land in the same slots.
+    const Item *ui = pl.ditems.as<Item>() + progs.back()->update_off;
+    const int un = progs.back()->update_n;
+    const Lv<double> *L64 = pl.outer64.as<Lv<double>>();
+    const Lv<float> *L32 = pl.fine32.as<Lv<float>>();
+    check_cuda(launch_ir_update(s, L64, L32, ui, un, pl.scales.as<double>(), pl.active.as<int>(),
+                                2),
                "ir_update");
-    count(pl);
-    ir_residual_norm(pl, 0, M, 0);
+    check_cuda(launch_ir_residual(s, L64, L32, ui, un, pl.scales.as<double>() + M,
+                                  pl.partials.as<double>(), 0, pl.active.as<int>(), 2,
+                                  pl.partials2.as<double>()),
+               "ir_residual");
+    check_cuda(launch_ir_track(s, L64, L32, ui, un, pl.scales.as<double>(), pl.active.as<int>(), M,
+                               pl.maxnz, pl.partials.as<double>(), pl.partials2.as<double>()),
+               "ir_track");
+    check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>(), M,
+                               pl.norms.as<double>(), 1, nullptr, nullptr),
+               "finalize");
+    check_cuda(launch_finalize(s, pl.partials2.as<double>(), pl.dfirst.as<int>(), M,
+                               pl.norms.as<double>() + M, 1, nullptr, nullptr),
+               "finalize");
+    count(pl, 5);
 }
 
 static void ir_step_graph(Plan &pl) {
@@ -1051,8 +1109,36 @@ void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph) {
     ir_push_state(pl, run);
     if (use_graph) ir_step_graph(pl);
     else ir_step(pl);
-    read_norms(pl, M);
+    read_norms(pl, 2 * M);
     p0.prof_collect(use_graph);
+    // Error bounds of the stored residual.  A tracked member whose bound is
+    // not below 0.1% of its residual (or whose residual is not finite) gets
+    // the residual recomputed in FP64 -- it replaces the tracked one -- and
+    // stays on the FP64 path for the rest of the solve.
+    std::vector<int> redo;
+    for (int m = 0; m < M; ++m) {
+        MemberRun &r = *run[m];
+        if (!r.active) continue;
+        const double nrm = pl.host_norms[m], mag = pl.host_norms[M + m];
+        if (r.mode == 1) {
+            r.magx += mag;
+            r.errb += kErrTrack * mag + kErrRound * r.magx;
+            if (!(r.errb <= 1e-3 * nrm)) redo.push_back(m);
+        } else {
+            r.magx = mag;
+            r.errb = kErrFp64 * mag;
+        }
+    }
+    if (!redo.empty()) {
+        for (int m : redo) ir_residual_norm(pl, m, m + 1, 0);
+        read_norms(pl, 2 * M);
+        for (int m : redo) {
+            MemberRun &r = *run[m];
+            r.mode = 2;
+            r.magx = pl.host_norms[M + m];
+            r.errb = kErrFp64 * r.magx;
+        }
+    }
     for (int m = 0; m < M; ++m) {
         MemberRun &r = *run[m];
         if (!r.active) continue;
@@ -1375,6 +1461,7 @@ void ellsolve_default_opts(ellsolve_opts *o) {
     o->smoother = 0;
     o->precond = 0;
     o->fmg = 0;
+    o->refine = 0;
 }
 
 const char *ellsolve_last_error(void) { return t_last_error.c_str(); }
@@ -1426,6 +1513,7 @@ ellsolve_status ellsolve_create_profiles(const ellsolve_grid *grid, double omega
     if (o.smoother != 0 && o.smoother != 1) throw Error(ELLSOLVE_ERR_ARG, "smoother must be 0 or 1");
     if (o.precond < 0 || o.precond > 2) throw Error(ELLSOLVE_ERR_ARG, "precond must be 0, 1 or 2");
     if (o.fmg != 0 && o.fmg != 1) throw Error(ELLSOLVE_ERR_ARG, "fmg must be 0 or 1");
+    if (o.refine != 0 && o.refine != 1) throw Error(ELLSOLVE_ERR_ARG, "refine must be 0 or 1");
     auto h = std::make_unique<ellsolve_s>();
     h->build(*grid, omega2, lambda2, r_levels, o, static_cast<cudaStream_t>(stream), p_cell, q_face);
     *out = h.release();

@@ -104,6 +104,9 @@ struct Problem;
 // The launch program of a set of problems ("members") solved together: every
 // kernel of the V-cycle is one launch over the items of all members.
 struct Plan {
+    Plan() = default;
+    Plan(const Plan &) = delete;
+    Plan &operator=(const Plan &) = delete;
     std::vector<Problem *> mem;
     int precision = 1;
     std::vector<int> base;  // first descriptor of each member
@@ -120,9 +123,11 @@ struct Plan {
     int outer_off = 0, outer_n = 0;   // finest columns, lv = member
     int norm_off[2] = {0, 0}, norm_n = 0;  // finest columns, lv = descriptor, u[0] / u[1]
     std::vector<int> outer_first;     // per-member ranges of outer items
-    DevBuf dfirst, partials, norms, scales, counts, active;
+    DevBuf dfirst, partials, partials2, norms, scales, counts, active;
     std::vector<int> stage_active;
-    std::vector<double> host_norms;
+    std::vector<double> host_norms;       // [2 M]: norms, then magnitudes
+    double *hnorms = nullptr;             // pinned staging of the device norms [4 M]
+    size_t hnorms_n = 0;
     cudaGraphExec_t gexec = nullptr;
     int graph_launches = 0;
 
@@ -192,6 +197,10 @@ struct MemberRun {
     std::vector<double> hist;
     bool active = true;
     double scale_cur = 1.0, scale_next = 1.0;
+    // refinement residual: 1 tracked (double-float update), 2 recomputed in
+    // FP64; errb bounds |tracked - true residual| (2-norm), magx ~ || |A| |x| ||
+    int mode = 1;
+    double errb = 0.0, magx = 0.0;
 };
 
 void ir_bind(Plan &pl, const std::vector<MemberRun *> &run);
