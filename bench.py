@@ -314,7 +314,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {
             "workload": args.workload, "grid": ("cubed sphere 6x" if kind == 1 else "box ") +
             f"{n}x{n}", "nz": nz, "unknowns": N, "omega2": w2, "lambda": l2 ** 0.5,
-            "solver": "FP32 V-cycle (2/2 line-Jacobi, rho 0.8) in FP64 refinement, CUDA graph",
+            "solver": ("FP32 V-cycle (2/2 line-Jacobi, rho 0.8) in FP64 refinement with the "
+                       "tracked residual, CUDA graph"),
             "inner_cycles": args.inner_cycles,
             "autotuned_smoother_ctas_per_sm": tuned_ctas,
             "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
@@ -522,7 +523,7 @@ def run_serving(torch, stream, count, rate=200.0, budget=96 << 30, slots=16):
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
-KERNEL_REV = "smooth-v8-twisted"
+KERNEL_REV = "smooth-v9-twisted-tmem"
 
 
 def main():
