@@ -1750,9 +1750,17 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                                                       const int *__restrict__ sel, int want,
                                                       double *__restrict__ partials,
                                                       double *__restrict__ partials2) {
+    extern __shared__ float2 vs_sh[];  // MODE 1: (V_k hi, lo) [nz]
     const Item it = items[blockIdx.x];
     if (sel && sel[it.lv] != want) return;  // the whole block: one member
     const Lv<double> &d = L64[it.lv];
+    if (MODE == 1) {
+        for (int k = threadIdx.x; k < d.nz; k += kBlk) {
+            const ff v = split_ff(d.V[k]);
+            vs_sh[k] = make_float2(v.hi, v.lo);
+        }
+        __syncthreads();
+    }
     const int c = it.col0 + threadIdx.x;
     const int nc = d.ncol;
     double acc = 0.0, acc2 = 0.0;
@@ -1781,7 +1789,8 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                 for (int j = 0; j < B; ++j) {
                     const int k = k0 + j;
                     if (k < nz) {
-                        const ff AV = mul_ff(A, split_ff(__ldg(V + k)));
+                        const float2 v2 = vs_sh[k];
+                        const ff AV = mul_ff(A, ff{v2.x, v2.y});
                         const ff bk = mul_ff(AV, split_ff(fv[j]));
                         const size_t o = size_t(k) * nc + c;
                         const float h = __fmul_rn(bk.hi, sc);
@@ -1919,45 +1928,67 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
         float colsum = 0.f, magsum = 0.f;
         float e0 = __ldg(e + c);
         ff flux_lo = {0.f, 0.f};
-#pragma unroll 2
-        for (int k = 0; k < nz; ++k) {
-            const size_t o = size_t(k) * nc;
-            const float ep = k + 1 < nz ? __ldg(e + o + nc + c) : 0.f;
-            const float *row = e + o;
-            // s e - sum_q t_q e_q: the hi parts summed by TwoSum, every error
-            // and lo part collected in one float
-            const ff p0 = mul_ff_f(S, e0);
-            const ff p1 = mul_ff_f(neg_ff(T0), __ldg(row + col.nb.x));
-            const ff p2 = mul_ff_f(neg_ff(T1), __ldg(row + col.nb.y));
-            const ff p3 = mul_ff_f(neg_ff(T2), __ldg(row + col.nb.z));
-            const ff p4 = mul_ff_f(neg_ff(T3), __ldg(row + col.nb.w));
-            ff h = two_sum(p0.hi, p1.hi);
-            float err = __fadd_rn(__fadd_rn(p0.lo, p1.lo), h.lo);
-            ff t = two_sum(h.hi, p2.hi);
-            err = __fadd_rn(err, __fadd_rn(p2.lo, t.lo));
-            t = two_sum(t.hi, p3.hi);
-            err = __fadd_rn(err, __fadd_rn(p3.lo, t.lo));
-            t = two_sum(t.hi, p4.hi);
-            err = __fadd_rn(err, __fadd_rn(p4.lo, t.lo));
-            const ff hm = two_sum(t.hi, err);
-            const float2 v2 = Vh[k], g2 = gh[k + 1];
-            const ff Vk = {v2.x, v2.y}, gk1 = {g2.x, g2.y};
-            // vertical: face flux g_{k+1} (e_k - e_{k+1}), carried to the next level
-            const ff flux_hi = mul_ff(gk1, two_sum(e0, -ep));
-            const ff Ae = add_ff(mul_ff(Vk, hm), mul_ff(A, add_ff(flux_hi, neg_ff(flux_lo))));
-            const float2 r2 = rt[o + c];
-            const ff rn = add_ff({r2.x, r2.y}, neg_ff(Ae));
-            const float nh = __fmul_rn(rn.hi, ratio), nl = __fmul_rn(rn.lo, ratio);
-            rt[o + c] = make_float2(nh, nl);
-            r32[o + c] = nh;
-            colsum = __fmaf_rn(rn.hi, rn.hi, colsum);
-            const float mag = __fmaf_rn(
-                v2.x, (fabsf(p0.hi) + fabsf(p1.hi)) + (fabsf(p2.hi) + (fabsf(p3.hi) + fabsf(p4.hi))),
-                A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
-            magsum = __fmaf_rn(mag, mag, magsum);
-            x[o + c] += f32_to_f64_pow2(e0, kx);
-            flux_lo = flux_hi;
-            e0 = ep;
+        // the loads of kTB levels are issued before their arithmetic
+        constexpr int kTB = 4;
+        for (int k0 = 0; k0 < nz; k0 += kTB) {
+            float ev[kTB], ew[kTB], ee[kTB], es[kTB], en[kTB];
+            float2 rv[kTB];
+            double xv[kTB];
+#pragma unroll
+            for (int j = 0; j < kTB; ++j) {
+                const int k = min(k0 + j, nz - 1);
+                const size_t o = size_t(k) * nc;
+                const float *row = e + o;
+                ev[j] = k + 1 < nz ? __ldg(row + nc + c) : 0.f;  // e_{k+1}
+                ew[j] = __ldg(row + col.nb.x);
+                ee[j] = __ldg(row + col.nb.y);
+                es[j] = __ldg(row + col.nb.z);
+                en[j] = __ldg(row + col.nb.w);
+                rv[j] = rt[o + c];
+                xv[j] = x[o + c];
+            }
+#pragma unroll
+            for (int j = 0; j < kTB; ++j) {
+                const int k = k0 + j;
+                if (k >= nz) break;
+                const size_t o = size_t(k) * nc;
+                const float ep = ev[j];
+                // s e - sum_q t_q e_q: the hi parts summed by TwoSum, every
+                // error and lo part collected in one float
+                const ff p0 = mul_ff_f(S, e0);
+                const ff p1 = mul_ff_f(neg_ff(T0), ew[j]);
+                const ff p2 = mul_ff_f(neg_ff(T1), ee[j]);
+                const ff p3 = mul_ff_f(neg_ff(T2), es[j]);
+                const ff p4 = mul_ff_f(neg_ff(T3), en[j]);
+                ff t = two_sum(p0.hi, p1.hi);
+                float err = __fadd_rn(__fadd_rn(p0.lo, p1.lo), t.lo);
+                t = two_sum(t.hi, p2.hi);
+                err = __fadd_rn(err, __fadd_rn(p2.lo, t.lo));
+                t = two_sum(t.hi, p3.hi);
+                err = __fadd_rn(err, __fadd_rn(p3.lo, t.lo));
+                t = two_sum(t.hi, p4.hi);
+                err = __fadd_rn(err, __fadd_rn(p4.lo, t.lo));
+                const ff hm = two_sum(t.hi, err);
+                const float2 v2 = Vh[k], g2 = gh[k + 1];
+                const ff Vk = {v2.x, v2.y}, gk1 = {g2.x, g2.y};
+                // vertical: face flux g_{k+1} (e_k - e_{k+1}), carried to the next level
+                const ff flux_hi = mul_ff(gk1, two_sum(e0, -ep));
+                const ff Ae =
+                    add_ff(mul_ff(Vk, hm), mul_ff(A, add_ff(flux_hi, neg_ff(flux_lo))));
+                const ff rn = add_ff({rv[j].x, rv[j].y}, neg_ff(Ae));
+                const float nh = __fmul_rn(rn.hi, ratio), nl = __fmul_rn(rn.lo, ratio);
+                rt[o + c] = make_float2(nh, nl);
+                r32[o + c] = nh;
+                colsum = __fmaf_rn(rn.hi, rn.hi, colsum);
+                const float mag = __fmaf_rn(
+                    v2.x,
+                    (fabsf(p0.hi) + fabsf(p1.hi)) + (fabsf(p2.hi) + (fabsf(p3.hi) + fabsf(p4.hi))),
+                    A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
+                magsum = __fmaf_rn(mag, mag, magsum);
+                x[o + c] = xv[j] + f32_to_f64_pow2(e0, kx);
+                flux_lo = flux_hi;
+                e0 = ep;
+            }
         }
         acc = double(colsum);
         acc2 = double(magsum);
@@ -2444,14 +2475,18 @@ cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned 
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
                                double *partials, int x_is_zero, const int *sel, int want,
-                               double *partials2) {
+                               double *partials2, int max_nz) {
     if (nitems <= 0) return cudaSuccess;
     if (x_is_zero == 2)
         k_ir_residual<2><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
                                                  partials2);
-    else if (x_is_zero)
-        k_ir_residual<1><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
-                                                 partials2);
+    else if (x_is_zero) {
+        const size_t bytes = size_t(max_nz) * sizeof(float2);
+        cudaError_t e = set_smem(k_ir_residual<1>, bytes);
+        if (e != cudaSuccess) return e;
+        k_ir_residual<1><<<nitems, kBlk, bytes, s>>>(L64, L32, items, scale, sel, want, partials,
+                                                     partials2);
+    }
     else
         k_ir_residual<0><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
                                                  partials2);

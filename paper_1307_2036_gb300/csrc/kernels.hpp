@@ -65,7 +65,8 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 //   magnitude of |A| |x| (bound on the rounding of the evaluation).
 // x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve;
 // r and its norm only); 2 the same but only the norm (nothing written).
-// sel: when not null, only members with sel[m] == want take part.
+// sel: when not null, only members with sel[m] == want take part.  max_nz:
+// the largest nz among the members.
 // Row-staged FP32 residual + restriction; every fine level of the launch has
 // n % 64 == 0.
 cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item *items,
@@ -74,7 +75,7 @@ cudaError_t launch_selftest_conv(cudaStream_t s, unsigned long long n, unsigned 
 cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                                const Item *items, int nitems, const double *scale,
                                double *partials, int x_is_zero, const int *sel, int want,
-                               double *partials2);
+                               double *partials2, int max_nz);
 // x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with sel[m] == want
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,

@@ -947,7 +947,8 @@ static void ir_residual_norm(Plan &pl, int m0, int m1, int x_is_zero) {
     check_cuda(launch_ir_residual(s, pl.outer64.as<Lv<double>>(), pl.fine32.as<Lv<float>>(),
                                   pl.ditems.as<Item>() + pl.outer_off + i0, i1 - i0,
                                   pl.scales.as<double>() + M, pl.partials.as<double>() + i0,
-                                  x_is_zero, nullptr, 0, pl.partials2.as<double>() + i0),
+                                  x_is_zero, nullptr, 0, pl.partials2.as<double>() + i0,
+                                  pl.maxnz),
                "ir_residual");
     check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>() + m0, m1 - m0,
                                pl.norms.as<double>() + m0, 1, nullptr, nullptr),
@@ -1031,7 +1032,7 @@ static void ir_step(Plan &pl) {
                "ir_update");
     check_cuda(launch_ir_residual(s, L64, L32, ui, un, pl.scales.as<double>() + M,
                                   pl.partials.as<double>(), 0, pl.active.as<int>(), 2,
-                                  pl.partials2.as<double>()),
+                                  pl.partials2.as<double>(), pl.maxnz),
                "ir_residual");
     check_cuda(launch_ir_track(s, L64, L32, ui, un, pl.scales.as<double>(), pl.active.as<int>(), M,
                                pl.maxnz, pl.partials.as<double>(), pl.partials2.as<double>()),
