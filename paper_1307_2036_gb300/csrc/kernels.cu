@@ -1342,6 +1342,11 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
     const int ncc = dc.ncol;
     if (C >= ncc) return;
     const int nz = d.nz, nf = d.n, ncn = dc.n, nc = d.ncol;
+    // levels [kb, ke) of the column: one chunk per blockIdx.y (small levels
+    // are split along the vertical so that enough threads wait on memory)
+    const int KC = (nz + int(gridDim.y) - 1) / int(gridDim.y);
+    const int kb = int(blockIdx.y) * KC, ke = min(nz, kb + KC);
+    if (kb >= ke) return;
     const int I = C % ncn, t = C / ncn, J = t % ncn, p = t / ncn;
     // children 0: (2I, 2J), 1: (2I+1, 2J), 2: (2I, 2J+1), 3: (2I+1, 2J+1)
     const int f0 = (p * nf + 2 * J) * nf + 2 * I;
@@ -1360,7 +1365,7 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
     const size_t snc = size_t(nc);
     auto issue = [&](int k) {
         T *sl = ring + (k % R) * 16 * kBlk;
-        const bool ok = k < nz, ok1 = k + 1 < nz;
+        const bool ok = k < ke, ok1 = ok && k + 1 < nz;
         const size_t o = ok ? size_t(k) * snc : 0, o1 = ok1 ? size_t(k + 1) * snc : 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1372,16 +1377,16 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
         cp_async_commit();
     };
 #pragma unroll 1
-    for (int k = 0; k < R - 1; ++k) issue(k);
+    for (int k = kb; k < kb + R - 1; ++k) issue(k);
     T u0[4], um[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        u0[q] = __ldg(u + fc[q]);
-        um[q] = T(0);
+        u0[q] = __ldg(u + size_t(kb) * snc + fc[q]);
+        um[q] = kb > 0 ? __ldg(u + size_t(kb - 1) * snc + fc[q]) : T(0);
     }
-    T gk = __ldg(g);
+    T gk = __ldg(g + kb);
 #pragma unroll 1
-    for (int k = 0; k < nz; ++k) {
+    for (int k = kb; k < ke; ++k) {
         cp_async_wait<R - 2>();
         const T *sl = ring + (k % R) * 16 * kBlk;
         T up[4], bk[4], ex[8];
@@ -1670,11 +1675,14 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
     const T *__restrict__ uc = dc.u[it.in];
     T *__restrict__ uf = d.u[it.out];
     const bool onto_zero = it.zero;  // interpolation only: the fine iterate is zero
-    for (int k0 = 0; k0 < nz; k0 += kPB) {
+    // levels [kb, ke): one chunk per blockIdx.y
+    const int KC = (nz + int(gridDim.y) - 1) / int(gridDim.y);
+    const int kb = int(blockIdx.y) * KC, ke = min(nz, kb + KC);
+    for (int k0 = kb; k0 < ke; k0 += kPB) {
         T cx[kPB], cy[kPB], cz[kPB], cw[kPB], fv[kPB];
 #pragma unroll
         for (int j = 0; j < kPB; ++j) {
-            const int k = k0 + j < nz ? k0 + j : nz - 1;
+            const int k = k0 + j < ke ? k0 + j : ke - 1;
             const T *row = uc + size_t(k) * ncc;
             cx[j] = __ldg(row + s.x);
             cy[j] = __ldg(row + s.y);
@@ -1684,7 +1692,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
         }
 #pragma unroll
         for (int j = 0; j < kPB; ++j) {
-            if (k0 + j >= nz) break;
+            if (k0 + j >= ke) break;
             T e;
             if (mode == 1) e = cx[j];
             else if (!corner) e = (T(9) * cx[j] + T(3) * cy[j] + T(3) * cz[j] + cw[j]) * T(0.0625);
@@ -2400,13 +2408,26 @@ cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int 
     return cudaGetLastError();
 }
 
+// Level chunks for a launch of nitems column blocks: small launches are split
+// along the vertical (chunks of at least 8 levels) until about four blocks per
+// SM exist; large ones run every column whole.
+static int level_chunks(int nitems, int max_nz) {
+    const int want = 4 * 152;
+    if (nitems >= want || max_nz < 16) return 1;
+    const int by_size = (want + nitems - 1) / nitems;
+    const int by_depth = max_nz / 8;
+    return by_size < by_depth ? by_size : by_depth;
+}
+
 template <typename T>
-cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems) {
+cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
+                                  int max_nz) {
     if (nitems <= 0) return cudaSuccess;
     const size_t bytes = size_t(restrict_ring<T>()) * 16 * kBlk * sizeof(T);
     cudaError_t e = set_smem(k_restrict_resid<T>, bytes);
     if (e != cudaSuccess) return e;
-    k_restrict_resid<T><<<nitems, kBlk, bytes, s>>>(L, items);
+    const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz)));
+    k_restrict_resid<T><<<grid, kBlk, bytes, s>>>(L, items);
     return cudaGetLastError();
 }
 
@@ -2429,9 +2450,10 @@ cudaError_t launch_restrict_rhs(cudaStream_t s, const Lv<T> *L, const Item *item
 
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
-                               int mode) {
+                               int mode, int max_nz) {
     if (nitems <= 0) return cudaSuccess;
-    k_prolong_add<T><<<nitems, kBlk, 0, s>>>(L, items, mode);
+    const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz)));
+    k_prolong_add<T><<<grid, kBlk, 0, s>>>(L, items, mode);
     return cudaGetLastError();
 }
 
@@ -2573,10 +2595,10 @@ cudaError_t launch_cg_scalars(cudaStream_t s, double *scalars, const double *sum
     template cudaError_t launch_resid<T>(cudaStream_t, const Lv<T> *, const Item *, int, int,    \
                                          double *);                                              \
     template cudaError_t launch_restrict_resid<T>(cudaStream_t, const Lv<T> *, const Item *,     \
-                                                  int);                                          \
+                                                  int, int);                                     \
     template cudaError_t launch_restrict_rhs<T>(cudaStream_t, const Lv<T> *, const Item *, int);  \
     template cudaError_t launch_prolong_add<T>(cudaStream_t, const Lv<T> *, const Item *, int,   \
-                                               int);                                             \
+                                               int, int);                                        \
     template cudaError_t launch_form_rhs<T>(cudaStream_t, const Lv<T> *, const Item *, int,      \
                                             const double *, T *, double *);
 ELLS_INST(float)

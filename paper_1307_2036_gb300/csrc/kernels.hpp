@@ -42,9 +42,11 @@ cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int 
                          double *partials);
 
 // b of descriptor lv+1 = 2x2 sums of (b - A u[in]) on descriptor lv.  Items
-// run over the coarse columns.
+// run over the coarse columns; max_nz: the largest nz among them (small
+// launches are split along the vertical).
 template <typename T>
-cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems);
+cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
+                                  int max_nz);
 
 // b of descriptor lv+1 = 2x2 sums of b on descriptor lv (full multigrid).
 // Items run over the coarse columns.
@@ -56,7 +58,7 @@ cudaError_t launch_restrict_rhs(cudaStream_t s, const Lv<T> *L, const Item *item
 // 1 constant.
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
-                               int mode);
+                               int mode, int max_nz);
 
 // Iterative-refinement outer step, per member m (items' lv = member index):
 //   r = A_P V_k f - A x   in FP64, f = L64[m].b (pointwise), x = L64[m].u[0],

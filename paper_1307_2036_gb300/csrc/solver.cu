@@ -548,7 +548,7 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
                 // one launch for the levels the row-staged kernel takes, one for the rest
                 std::vector<std::pair<int, int>> rows_pre, other_pre;
                 for (auto ml : pre)
-                    (precision == 1 && restrict_rows_eligible(*mem[ml.first], ml.second)
+                    (precision == 1 && restrict_rows_preferred(*mem[ml.first], ml.second)
                          ? rows_pre
                          : other_pre)
                         .push_back(ml);
@@ -642,6 +642,13 @@ bool restrict_rows_eligible(const Problem &p, int level) {
     return level + 1 < p.nlev && p.lev[level].n % 64 == 0;
 }
 
+// The V-cycle takes the row-staged restriction where it fills the GPU (at
+// least four column blocks per SM); smaller levels take the per-thread kernel
+// split along the vertical, which is latency-bound for a shorter time.
+bool restrict_rows_preferred(const Problem &p, int level) {
+    return restrict_rows_eligible(p, level) && p.lev[level + 1].ncol >= 4 * 152 * kBlk;
+}
+
 bool rows_eligible(const Problem &p, int level) {
     const LevelStore &Ls = p.lev[level];
     if (Ls.n % 4 != 0 || Ls.ncol % 4 != 0) return false;
@@ -710,7 +717,7 @@ static void run_program(Plan &pl, const Program &prog) {
                                                     it + op.off, op.n),
                                "restrict_rows");
                 else
-                    check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n), "restrict");
+                    check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n, pl.maxnz), "restrict");
                 count(pl);
                 break;
             case Op::kRestrictRhs:
@@ -718,7 +725,7 @@ static void run_program(Plan &pl, const Program &prog) {
                 count(pl);
                 break;
             case Op::kProlong:
-                check_cuda(launch_prolong_add<T>(s, L, it + op.off, op.n, o.prolong), "prolong");
+                check_cuda(launch_prolong_add<T>(s, L, it + op.off, op.n, o.prolong, pl.maxnz), "prolong");
                 count(pl);
                 break;
             case Op::kMemset: {
@@ -1412,10 +1419,12 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
                                                 div_up(p.lev[level + 1].ncol, kBlk)),
                            "restrict_rows");
             else
-                check_cuda(launch_restrict_resid<T>(s, L, it, div_up(p.lev[level + 1].ncol, kBlk)),
+                check_cuda(launch_restrict_resid<T>(s, L, it, div_up(p.lev[level + 1].ncol, kBlk), p.nz),
                            "restrict");
             break;
-        case 4: check_cuda(launch_prolong_add<T>(s, L, it, per, p.opts.prolong), "prolong"); break;
+        case 4:
+            check_cuda(launch_prolong_add<T>(s, L, it, per, p.opts.prolong, p.nz), "prolong");
+            break;
     }
     check_cuda(cudaStreamSynchronize(s), "level op sync");
     return ELLSOLVE_OK;

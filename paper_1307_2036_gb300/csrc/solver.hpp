@@ -215,6 +215,7 @@ void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Ite
                      double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned);
 bool rows_eligible(const Problem &p, int level);
 bool restrict_rows_eligible(const Problem &p, int level);
+bool restrict_rows_preferred(const Problem &p, int level);
 
 ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
                          const std::vector<double *> &x, double rtol, int maxit,
