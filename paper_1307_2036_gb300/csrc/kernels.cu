@@ -2099,6 +2099,14 @@ __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ par
     }
 }
 
+// Copy of n doubles by the SMs (into mapped pinned host memory: the copy
+// engines may be busy with the caller's large transfers, behind which a small
+// cudaMemcpyAsync would wait).
+__global__ void __launch_bounds__(256) k_copy_doubles(const double *__restrict__ src,
+                                                      double *__restrict__ dst, int n) {
+    for (int i = threadIdx.x; i < n; i += 256) dst[i] = src[i];
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm PCG (FP64) with M = Dtilde.
 // ---------------------------------------------------------------------------
@@ -2547,6 +2555,12 @@ cudaError_t launch_finalize(cudaStream_t s, const double *partials, const int *f
                             double *out, int op, double *scale_out, const double *counts) {
     if (nmembers <= 0) return cudaSuccess;
     k_finalize<<<nmembers, 256, 0, s>>>(partials, first, out, op, scale_out, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_doubles(cudaStream_t s, const double *src, double *dst, int n) {
+    if (n <= 0) return cudaSuccess;
+    k_copy_doubles<<<1, 256, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,9 @@ cudaError_t launch_form_rhs(cudaStream_t s, const Lv<T> *L, const Item *items, i
 // .. first[m+1]) in a fixed order, for m < nmembers.  op 0: plain sum; op 1:
 // sqrt of the sum; op 2: as 1 and also scale_out[m] = sqrt(count)/norm when
 // scale_out != null.
+// dst[i] = src[i], i < n, by one block of SM threads (dst may be mapped host memory)
+cudaError_t launch_copy_doubles(cudaStream_t s, const double *src, double *dst, int n);
+
 cudaError_t launch_finalize(cudaStream_t s, const double *partials, const int *first, int nmembers,
                             double *out, int op, double *scale_out, const double *counts);
 

@@ -68,7 +68,6 @@ static void upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) {
 Problem::~Problem() {
     plan.reset();
     batch_plan.reset();
-    if (pinned) cudaFreeHost(pinned);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto &e : ev_free) cudaEventDestroy(e);
     for (auto &e : ev_graph) cudaEventDestroy(e);
@@ -259,9 +258,6 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
         e.b = L.b32.as<float>();
         e.aux = L.aux32.as<float>();
     }
-    check_cuda(cudaHostAlloc(reinterpret_cast<void **>(&pinned), 64 * sizeof(double),
-                             cudaHostAllocDefault),
-               "cudaHostAlloc");
     rebind(w2, l2, rl, pc, qf);
 }
 
@@ -400,8 +396,10 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
         if (hnorms) cudaFreeHost(hnorms);
         hnorms = nullptr;
         check_cuda(cudaHostAlloc(reinterpret_cast<void **>(&hnorms), size_t(4 * M) * sizeof(double),
-                                 cudaHostAllocDefault),
+                                 cudaHostAllocMapped),
                    "pinned norms");
+        check_cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&hnorms_dev), hnorms, 0),
+                   "mapped norms");
         hnorms_n = size_t(4 * M);
     }
     items_dirty = true;
@@ -789,13 +787,15 @@ void Problem::prof_collect(bool graph_replayed) {
 // ---------------------------------------------------------------------------
 // Solvers
 // ---------------------------------------------------------------------------
-// the first `count` (<= 2 M) device norms into host_norms
-static double read_norms(Plan &pl, int count) {
-    const int M = count;
+// The first `nvals` (<= 2 M) device norms into host_norms.  A kernel writes
+// them into mapped pinned memory: a device-to-host cudaMemcpyAsync would queue
+// behind whatever large transfer the caller has on the copy engines.
+static double read_norms(Plan &pl, int nvals) {
+    const int M = nvals;
     cudaStream_t s = pl.mem[0]->stream;
     double *h = pl.hnorms;
-    check_cuda(cudaMemcpyAsync(h, pl.norms.p, M * sizeof(double), cudaMemcpyDeviceToHost, s),
-               "norm copy");
+    check_cuda(launch_copy_doubles(s, pl.norms.as<double>(), pl.hnorms_dev, M), "norm copy");
+    count(pl);
     check_cuda(cudaStreamSynchronize(s), "norm sync");
     for (int m = 0; m < M; ++m) pl.host_norms[m] = h[m];
     return h[0];

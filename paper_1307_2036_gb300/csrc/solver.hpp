@@ -126,7 +126,8 @@ struct Plan {
     DevBuf dfirst, partials, partials2, norms, scales, counts, active;
     std::vector<int> stage_active;
     std::vector<double> host_norms;       // [2 M]: norms, then magnitudes
-    double *hnorms = nullptr;             // pinned staging of the device norms [4 M]
+    double *hnorms = nullptr;             // mapped pinned staging of the device norms [4 M]
+    double *hnorms_dev = nullptr;         // its device address
     size_t hnorms_n = 0;
     cudaGraphExec_t gexec = nullptr;
     int graph_launches = 0;
@@ -155,7 +156,6 @@ struct Problem {
     int fine_cur = 0;
     DevBuf cg[4], cg_scal;
     std::unique_ptr<Plan> plan, batch_plan;
-    double *pinned = nullptr;
     uint64_t launches = 0;
     bool capturing = false;
     // CUDA-event timing of the finest-level smoother launches
