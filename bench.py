@@ -306,6 +306,7 @@ def run_ours(args, rank, world, local_rank):
         extras["ensemble"] = run_ensemble(torch, stream)
         extras["serving"] = run_serving(torch, stream, args.serve_requests)
         extras["smoothers"] = run_smoothers(torch, stream, args.workload)
+        extras["configs"] = run_configs(torch, stream)
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns*V-cycles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -338,6 +339,68 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_configs(torch, stream):
+    """The small configurations beside the benchmark workload.  C1: box 32x32,
+    n_z = 32 uniform on [1, 1.01], omega^2 = 0.01, lambda = 1, seeded uniform
+    and manufactured (3, 5) x cos m = 2 right-hand sides, time to 1e-5 for FP64
+    multigrid, mixed precision and PCG (latency-bound: time to solution, not a
+    roofline).  C2: box 256x256, n_z = 64 graded, the 9 cases omega^2 x lambda
+    with a uniform right-hand side: FP64 multigrid and PCG to 1e-5, mixed
+    precision to 1e-10 (V-cycles or iterations, time, status)."""
+    import numpy as np
+
+    from paper_1307_2036_gb300 import ellsolve, inputs
+
+    def timed(sv, f, x, rtol, maxit):
+        sv.solve(f, x, rtol=rtol, maxit=maxit)  # warm-up (graph capture)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        st, res = sv.solve(f, x, rtol=rtol, maxit=maxit)
+        e1.record(stream)
+        stream.synchronize()
+        return {"ms": e0.elapsed_time(e1), "iterations": res.iterations,
+                "rel_residual": res.rel_residual, "status": int(st)}
+
+    solvers = (("fp64 multigrid", dict(precision=0), 1e-5, 100),
+               ("mixed multigrid", dict(precision=1, use_graph=1), 1e-5, 100),
+               ("fp64 pcg", dict(precision=0, solver=1), 1e-5, 2000))
+    out = {"C1": {"workload": "box 32x32x32 uniform, omega2 0.01, lambda 1, rtol 1e-5"}}
+    r1 = inputs.radial_levels(32)
+    for rhs_name, fh in (("uniform", inputs.uniform_pm1((32, 1, 32, 32))),
+                         ("manufactured", inputs.fourier_cos_mode(32, 32))):
+        with torch.cuda.stream(stream):
+            f = torch.from_numpy(np.ascontiguousarray(fh)).to("cuda")
+            x = torch.zeros_like(f)
+        stream.synchronize()
+        for name, kw, rtol, maxit in solvers:
+            sv = ellsolve.Solver(0, 32, 32, r1, 0.01, 1.0, stream=stream.cuda_stream, **kw)
+            out["C1"][f"{rhs_name}, {name}"] = timed(sv, f, x, rtol, maxit)
+            sv.close()
+    nb, nzb = 256, 64
+    rb = inputs.radial_levels(nzb, graded=True)
+    with torch.cuda.stream(stream):
+        fb = torch.from_numpy(rhs_for(0, nb, nzb, "uniform")).to("cuda")
+        xb = torch.zeros_like(fb)
+    stream.synchronize()
+    out["C2"] = {"workload": "box 256x256x64 graded, uniform RHS; multigrid and PCG to 1e-5, "
+                             "mixed precision to 1e-10", "cases": []}
+    for w2 in (1e-3, 1e-2, 1e-1):
+        for lam in (0.1, 1.0, 10.0):
+            case = {"omega2": w2, "lambda": lam}
+            for name, kw, rtol, maxit in solvers:
+                if name == "mixed multigrid":
+                    rtol = 1e-10
+                sv = ellsolve.Solver(0, nb, nzb, rb, w2, lam * lam, stream=stream.cuda_stream,
+                                     **kw)
+                case[name] = timed(sv, fb, xb, rtol, maxit)
+                sv.close()
+            out["C2"]["cases"].append(case)
+    del fb, xb
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_smoothers(torch, stream, workload, reps=3):

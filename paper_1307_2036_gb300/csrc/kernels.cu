@@ -2356,10 +2356,13 @@ static cudaError_t launch_tw_zfat(cudaStream_t s, const Lv<float> *L, const Item
     return cudaGetLastError();
 }
 
+// f' goes to tensor memory on launches of at least one CTA per SM; on the
+// small levels it stays in L2 anyway, and the TMEM allocation and release only
+// lengthen a latency-bound sweep.
 template <int Z, int FR, bool ALN>
 static cudaError_t launch_tw_zfa(cudaStream_t s, const Lv<float> *L, const Item *items,
                                  int nitems, float rho, int max_nz, int ctas_per_sm) {
-    if (max_nz <= kTwTmemMaxNz)
+    if (max_nz <= kTwTmemMaxNz && nitems >= 152)
         return launch_tw_zfat<Z, FR, ALN, true>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
     return launch_tw_zfat<Z, FR, ALN, false>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
