@@ -168,6 +168,37 @@ def aggregate_ranks(dist, ms, ms_e2e, cycles, e2e_cycles, device="cpu"):
     return float(tmax[0]), float(tmax[1]), float(tsum[2]), float(tsum[3])
 
 
+def bind_host_to_gpu(torch, dev):
+    """Run this process on the CPUs next to the GPU (its PCI device's
+    local_cpulist), so that pinned host buffers allocated afterwards sit in
+    that NUMA node and the copies do not cross sockets.  Returns the CPU list,
+    or None when the system does not say."""
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        dom = getattr(props, "pci_domain_id", 0)
+        bus = getattr(props, "pci_bus_id", None)
+        slot = getattr(props, "pci_device_id", None)
+        if bus is None or slot is None:
+            return None
+        path = f"/sys/bus/pci/devices/{dom:04x}:{bus:02x}:{slot:02x}.0/local_cpulist"
+        with open(path) as fh:
+            text = fh.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return text
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -175,6 +206,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_1307_2036_gb300 import ellsolve, inputs
 
     torch.cuda.set_device(local_rank)
+    host_cpus = bind_host_to_gpu(torch, local_rank)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -242,6 +274,19 @@ def run_ours(args, rank, world, local_rank):
         xd = [x, torch.zeros_like(x)]
     stream.synchronize()
     h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    # the copy bandwidth of this machine, alone (outside the timed region)
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0.record(h2d)
+    with torch.cuda.stream(h2d):
+        fd[1].copy_(f_host, non_blocking=True)
+    c1.record(h2d)
+    with torch.cuda.stream(h2d):
+        x_host.copy_(xd[1], non_blocking=True)
+    c2.record(h2d)
+    h2d.synchronize()
+    copy_gbs = (N * 8 / (c0.elapsed_time(c1) * 1e6), N * 8 / (c1.elapsed_time(c2) * 1e6))
+    solve_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_solved = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
@@ -263,7 +308,9 @@ def run_ours(args, rank, world, local_rank):
         stream.wait_event(ev_in[j])
         if i >= 2:
             stream.wait_event(ev_out[j])  # the solution of step i-2 has left this buffer
+        solve_ev[i][0].record(stream)
         st, res = sv.solve(fd[j], xd[j], rtol=rtol, maxit=60)
+        solve_ev[i][1].record(stream)
         if st < 0:
             raise RuntimeError(f"solve failed: {st}")
         e2e_cycles += res.iterations
@@ -277,6 +324,7 @@ def run_ours(args, rank, world, local_rank):
     h1.record(stream)
     barrier()
     ms_e2e = h0.elapsed_time(h1)
+    e2e_solve_ms = sum(a.elapsed_time(b) for a, b in solve_ev) / max(1, len(solve_ev))
     del fd, xd
 
     if dist is not None:
@@ -331,7 +379,10 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e, "unit": "unknowns*V-cycles/s", "h2d_bytes_per_step": N * 8,
                 "d2h_bytes_per_step": N * 8,
                 "copies": "pinned host <-> device on copy streams, double-buffered: step i+1's "
-                          "input and step i-1's output move during step i's solve"},
+                          "input and step i-1's output move during step i's solve",
+                "copy_gbs_alone": {"h2d": copy_gbs[0], "d2h": copy_gbs[1]},
+                "host_cpus": host_cpus,
+                "solve_ms_in_loop": e2e_solve_ms},
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
