@@ -1655,7 +1655,9 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
 // three cells meet at a cube corner, 1/2, 1/4, 1/4.  The loads of kPB levels
 // are issued before their arithmetic and stores, so each thread keeps 5 kPB
 // loads in flight.  Items flagged zero interpolate onto a zero fine iterate
-// (the start of each level of full multigrid) without reading it.
+// (the start of each level of full multigrid) without reading it.  The fine
+// values are read and written once, with evict-first hints, so that the
+// coarse values, which the neighbouring fine cells gather again, stay in L2.
 // ---------------------------------------------------------------------------
 constexpr int kPB = 8;
 
@@ -1688,7 +1690,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
             cy[j] = __ldg(row + s.y);
             cz[j] = __ldg(row + s.z);
             cw[j] = __ldg(row + sw);
-            fv[j] = onto_zero ? T(0) : uf[size_t(k) * nc + f];
+            fv[j] = onto_zero ? T(0) : __ldcs(uf + size_t(k) * nc + f);
         }
 #pragma unroll
         for (int j = 0; j < kPB; ++j) {
@@ -1697,7 +1699,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
             if (mode == 1) e = cx[j];
             else if (!corner) e = (T(9) * cx[j] + T(3) * cy[j] + T(3) * cz[j] + cw[j]) * T(0.0625);
             else e = (T(2) * cx[j] + cy[j] + cz[j]) * T(0.25);
-            uf[size_t(k0 + j) * nc + f] = fv[j] + e;
+            __stcs(uf + size_t(k0 + j) * nc + f, fv[j] + e);
         }
     }
 }
