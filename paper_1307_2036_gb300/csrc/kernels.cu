@@ -1954,8 +1954,8 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                 ee[j] = __ldg(row + col.nb.y);
                 es[j] = __ldg(row + col.nb.z);
                 en[j] = __ldg(row + col.nb.w);
-                rv[j] = rt[o + c];
-                xv[j] = x[o + c];
+                rv[j] = __ldcs(rt + o + c);  // x and rt: not needed before the next step
+                xv[j] = __ldcs(x + o + c);
             }
 #pragma unroll
             for (int j = 0; j < kTB; ++j) {
@@ -1987,7 +1987,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                     add_ff(mul_ff(Vk, hm), mul_ff(A, add_ff(flux_hi, neg_ff(flux_lo))));
                 const ff rn = add_ff({rv[j].x, rv[j].y}, neg_ff(Ae));
                 const float nh = __fmul_rn(rn.hi, ratio), nl = __fmul_rn(rn.lo, ratio);
-                rt[o + c] = make_float2(nh, nl);
+                __stcs(rt + o + c, make_float2(nh, nl));
                 r32[o + c] = nh;
                 colsum = __fmaf_rn(rn.hi, rn.hi, colsum);
                 const float mag = __fmaf_rn(
@@ -1995,7 +1995,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                     (fabsf(p0.hi) + fabsf(p1.hi)) + (fabsf(p2.hi) + (fabsf(p3.hi) + fabsf(p4.hi))),
                     A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
                 magsum = __fmaf_rn(mag, mag, magsum);
-                x[o + c] = xv[j] + f32_to_f64_pow2(e0, kx);
+                __stcs(x + o + c, xv[j] + f32_to_f64_pow2(e0, kx));
                 flux_lo = flux_hi;
                 e0 = ep;
             }
