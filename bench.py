@@ -274,7 +274,11 @@ def run_ours(args, rank, world, local_rank):
         xd = [x, torch.zeros_like(x)]
     stream.synchronize()
     h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
-    # the copy bandwidth of this machine, alone (outside the timed region)
+    # the copy bandwidth of this machine, alone (outside the timed region; one
+    # untimed copy each way first, so that first-touch costs are not counted)
+    with torch.cuda.stream(h2d):
+        fd[1].copy_(f_host, non_blocking=True)
+        x_host.copy_(xd[1], non_blocking=True)
     c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     c0.record(h2d)
     with torch.cuda.stream(h2d):
