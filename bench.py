@@ -359,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
         extras["serving"] = run_serving(torch, stream, args.serve_requests)
         extras["smoothers"] = run_smoothers(torch, stream, args.workload)
         extras["configs"] = run_configs(torch, stream)
+        extras["accuracy"] = run_accuracy(torch, stream, args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns*V-cycles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -394,6 +395,42 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_accuracy(torch, stream, workload):
+    """The benchmark workload solved to 1e-10 in mixed precision and to 1e-12
+    by the FP64 multigrid (whose results match the oracle's to 1e-10 in the
+    parity tests): relative L2 difference of the two solutions, with times."""
+    from paper_1307_2036_gb300 import ellsolve, inputs
+    kind, n, nz, graded, w2, l2, rhs_kind, _ = WORKLOADS[workload]
+    r = inputs.radial_levels(nz, graded=graded)
+    with torch.cuda.stream(stream):
+        f = torch.from_numpy(rhs_for(kind, n, nz, rhs_kind)).to("cuda")
+        xm = torch.zeros_like(f)
+        x64 = torch.zeros_like(f)
+    stream.synchronize()
+    out = {"workload": f"{workload}: mixed precision to 1e-10 against FP64 multigrid to 1e-12"}
+    for name, x, kw, rtol in (("mixed", xm, dict(precision=1, use_graph=1), 1e-10),
+                              ("fp64", x64, dict(precision=0), 1e-12)):
+        sv = ellsolve.Solver(kind, n, nz, r, w2, l2, stream=stream.cuda_stream, **kw)
+        if name == "mixed":
+            sv.autotune()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        st, res = sv.solve(f, x, rtol=rtol, maxit=100)
+        e1.record(stream)
+        stream.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "vcycles": res.iterations,
+                     "rel_residual": res.rel_residual, "status": int(st)}
+        sv.close()
+    with torch.cuda.stream(stream):
+        err = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
+    stream.synchronize()
+    out["rel_l2_mixed_vs_fp64"] = err
+    del f, xm, x64
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_configs(torch, stream):
