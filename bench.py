@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -67,7 +68,7 @@ class ClockSampler:
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
-        out = os.environ.get("ELLSOLVE_CLOCKS_DIR", os.path.join(ROOT, "gpurun_out"))
+        out = os.environ.get("ELLSOLVE_CLOCKS_DIR", tempfile.gettempdir())
         self.path = os.path.join(out, f"clocks_rank{device_index}.csv")
 
     def start(self):

@@ -92,7 +92,7 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
             it.colour = (unsigned char)(rb ? parity + 1 : 0);
         }
     cudaStream_t s = p.stream;
-    // pageable sources: the copies are staged by the driver, nothing is allocated
+    // pageable sources: the CUDA driver stages the copies, nothing is allocated here
     check_cuda(cudaMemcpyAsync(base, &d, sizeof(d), cudaMemcpyHostToDevice, s), "descriptor");
     check_cuda(cudaMemcpyAsync(base + off_items, items.data(), items.size() * sizeof(Item),
                                cudaMemcpyHostToDevice, s),
