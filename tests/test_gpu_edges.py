@@ -115,6 +115,10 @@ def test_invalid_arguments_rejected(torch_mod):
         dict(kind=1, n=8, nz=8, r_levels=r, omega2=0.0),
         dict(kind=1, n=8, nz=8, r_levels=r, solver=1, precision=1),
         dict(kind=1, n=8, nz=8, r_levels=r, damping=2.5),
+        dict(kind=1, n=8, nz=8, r_levels=r, smoother=2),
+        dict(kind=1, n=8, nz=8, r_levels=r, solver=1, precond=3),
+        dict(kind=1, n=8, nz=8, r_levels=r, fmg=2),
+        dict(kind=1, n=8, nz=8, r_levels=r, precision=1, refine=2),
     ]
     for kw in bad:
         args = dict(omega2=0.01, lambda2=1.0)
