@@ -93,3 +93,18 @@ def test_fmg_batch_mixed_levels(torch_mod, oracle_mod):
         assert res.rel_residual <= 1e-10
         u_ref = p.og.mg_solve(p.og.volumes() * f, rtol=1e-13, maxit=80)[0]
         assert rel_l2(p.host(x), u_ref) <= 1e-9
+
+
+def test_batch_rejects_mixed_fmg(torch_mod, oracle_mod):
+    """Members of one batch share the launch sequence, so full multigrid is
+    all or nothing."""
+    from paper_1307_2036_gb300 import ellsolve
+    a = pair(oracle_mod, CASES[0], precision=1)
+    c = CASES[0]
+    b = Pair(oracle_mod, c[0], c[1], c[2], omega2=c[5], lambda2=c[6], graded=c[3],
+             mapping=c[4], precision=1, fmg=0)
+    fs = [inputs.uniform_pm1(p.og.shape(), member=520 + i) for i, p in enumerate((a, b))]
+    xs = [a.empty(), b.empty()]
+    with pytest.raises(ellsolve.EllsolveError) as e:
+        ellsolve.solve_batch([a.sv, b.sv], [a.dev(fs[0]), b.dev(fs[1])], xs, rtol=1e-8, maxit=10)
+    assert e.value.status == ellsolve.ERR_ARG
