@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from paper_1307_2036_gb300 import inputs
-from gpu_util import Pair, fp64_tol, rel_l2, require_gpu
+from gpu_util import Pair, fp64_tol, rel_l2, require_gpu, sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -28,8 +28,9 @@ CASES = [
     (1, 12, 16, True, 0, 0.01, 1.0),     # equiangular sphere, 864 columns
     (1, 16, 8, False, 1, 0.05, 0.25),    # equidistant sphere, 3 levels
     (1, 8, 128, True, 0, 0.01, 1.0),     # the 128-level graded column of the sphere configs
+    (0, 12, 19, True, 0, 0.02, 4.0),     # n_z = 19: small levels split into 10 + 9 levels
 ]
-IDS = ["box24", "box20g", "sph12", "sph16e", "sph8z128"]
+IDS = ["box24", "box20g", "sph12", "sph16e", "sph8z128", "box12z19"]
 
 
 @pytest.fixture(scope="module")
@@ -193,7 +194,11 @@ def test_vcycles_fp64_fixed_count(torch_mod, oracle_mod, case):
     u4, it, hist = p.og.mg_solve(b, rtol=0.0, maxit=4)
     assert res.iterations == 4 and it == 4
     assert rel_l2(p.host(x), u4) <= tol
-    assert abs(res.rel_residual - hist[-1]) <= 1e-6 * hist[-1] + 1e-15
+    # near the attainable residual two correct FP64 evaluations of b - A x
+    # differ by the rounding of the cancelling sum: 16x the oracle's own
+    # sensitivity of the residual to ulp-level changes of x
+    rfloor = 16.0 * sensitivity(lambda uu: p.og.residual(b, uu), u4) * hist[-1]
+    assert abs(res.rel_residual - hist[-1]) <= 1e-6 * hist[-1] + rfloor + 1e-15
 
 
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
