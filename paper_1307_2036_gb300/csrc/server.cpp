@@ -160,8 +160,7 @@ void ellsolve_server_s::run_worker() {
                     mem.push_back(q->prob.get());
                     run.push_back(&q->run);
                 }
-                plan.reset();
-                plan = std::make_unique<Plan>();
+                if (!plan) plan = std::make_unique<Plan>();
                 plan->build(mem, 1);
                 ir_bind(*plan, run);
                 const int m0 = int(active.size() - joined.size());

@@ -26,6 +26,10 @@ thread_local std::string t_last_error;
 void set_last_error(const std::string &m) { t_last_error = m; }
 
 void DevBuf::alloc(size_t b) {
+    if (p && b <= cap) {
+        bytes = b;
+        return;
+    }
     reset();
     if (b == 0) return;
     cudaError_t e = cudaMalloc(&p, b);
@@ -35,13 +39,13 @@ void DevBuf::alloc(size_t b) {
         throw Error(e == cudaErrorMemoryAllocation ? ELLSOLVE_ERR_NOMEM : ELLSOLVE_ERR_CUDA,
                     "cudaMalloc(" + std::to_string(b) + " bytes): " + cudaGetErrorString(e));
     }
-    bytes = b;
+    bytes = cap = b;
 }
 
 void DevBuf::reset() {
     if (p) cudaFree(p);
     p = nullptr;
-    bytes = 0;
+    bytes = cap = 0;
 }
 
 void check_cuda(cudaError_t e, const char *what) {
@@ -333,7 +337,10 @@ void Plan::drop_graph() {
     gexec = nullptr;
 }
 
+// (Re)build for a set of members; the device buffers of an earlier build are
+// reused where large enough.
 void Plan::build(const std::vector<Problem *> &members, int prec) {
+    drop_graph();
     mem = members;
     precision = prec;
     const int M = int(mem.size());

@@ -24,23 +24,27 @@ void check_cuda(cudaError_t e, const char *what);
 void set_last_error(const std::string &m);
 
 // Owning device allocation.
+// A device allocation.  alloc() keeps the current block when it is large
+// enough (bytes is the size asked for, cap the size allocated), so that plans
+// rebuilt for a changed batch do not free and allocate again.
 struct DevBuf {
     void *p = nullptr;
-    size_t bytes = 0;
+    size_t bytes = 0, cap = 0;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), cap(o.cap) {
         o.p = nullptr;
-        o.bytes = 0;
+        o.bytes = o.cap = 0;
     }
     DevBuf &operator=(DevBuf &&o) noexcept {
         if (this != &o) {
             reset();
             p = o.p;
             bytes = o.bytes;
+            cap = o.cap;
             o.p = nullptr;
-            o.bytes = 0;
+            o.bytes = o.cap = 0;
         }
         return *this;
     }
