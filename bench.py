@@ -379,8 +379,10 @@ def run_ours(args, rank, world, local_rank):
             tinfo = json.load(fh)
         if tinfo.get("workload") == args.workload and tinfo.get("kernel_rev") == KERNEL_REV:
             traffic = tinfo.get("dram_bytes_per_launch")
+    # the oracle's CPU baseline: rank 0 of a single-GPU run only
     cpu_rate, cpu_s, cpu_cores, cpu_desc = (oracle_rate_parallel(ORACLE_SAMPLE, 1)
-                                            if not args.no_cpu else (None, 0, 1, ""))
+                                            if not args.no_cpu and world == 1
+                                            else (None, 0, 1, ""))
     extras = {}
     if not args.no_extras:
         del sv
