@@ -195,11 +195,13 @@ ellsolve_status ellsolve_level_prolong_add(ellsolve_t h, int level, int fp32, co
                                            void *u);
 
 /* ellsolve_level_smooth for callers that cannot allocate device memory (the
- * paper has no counterpart: this is a deployment variant).  Examples: code
- * running while its stream is captured into a CUDA graph, callers whose device
- * memory is owned by their own allocator under a fixed budget, and latency-
- * critical loops where cudaMalloc could synchronise the device.  It runs the
- * same kernels as ellsolve_level_smooth and gives the same result, but takes
+ * paper has no counterpart: this is a deployment variant).  Such callers are,
+ * for example, host programs that give the library a fixed device-memory
+ * budget owned by their own allocator or memory pool (a cudaMalloc outside
+ * that pool would overrun the budget, or fail once the pool holds the memory),
+ * and latency-critical loops where a cudaMalloc / cudaFree pair could
+ * synchronise the device.  It runs the same kernels as ellsolve_level_smooth
+ * with the same work items and gives the same result bit for bit, but takes
  * its scratch (the partner iterate, the Thomas coefficients, the level
  * descriptor and the work items) from one 64 MiB array that the library holds
  * in static device memory on every GPU where it is loaded, until the process
@@ -208,13 +210,16 @@ ellsolve_status ellsolve_level_prolong_add(ellsolve_t h, int level, int fp32, co
  *    2 * unknowns * sizeof(element) + 4 KB; larger levels return
  *    ELLSOLVE_ERR_CAPACITY with a message.  Nothing in the array needs to
  *    start at zero: every scratch value is written before it is read.
+ *  - The device current at the call must be the one current when the handle
+ *    was created (ELLSOLVE_ERR_ARG otherwise): the array is per device.
  *  - The first call on a device looks up the array's device address with
  *    cudaGetSymbolAddress (once per device, with that device current); make
  *    that first call before any stream capture on the device.
  *  - All calls on a device share the one array and it keeps the last call's
  *    contents, so calls whose work overlaps on the GPU (from several host
  *    threads or streams) race and must be serialised by the caller.
- *  - The call synchronises the handle's stream before returning. */
+ *  - The descriptor and work items are copied from host memory, and the call
+ *    waits for the handle's stream before returning. */
 ellsolve_status ellsolve_level_smooth_noalloc(ellsolve_t h, int level, int fp32, const void *b,
                                               void *u, int nsweeps, double rho);
 

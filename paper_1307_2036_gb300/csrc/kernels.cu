@@ -300,30 +300,6 @@ __global__ void __launch_bounds__(kBlk) k_smooth(const Lv<T> *__restrict__ L,
     cp_async_wait<0>();
 }
 
-// ---------------------------------------------------------------------------
-// Line smoother, row-staged variant for FP32 levels with n % 4 == 0,
-// ncol % 4 == 0 and nz % 8 == 0 (every fine level of the configurations).
-//
-// Same sweep and arithmetic as k_smooth, with the data movement organised per
-// warp: for level k a warp (32 consecutive columns) needs its own row of u
-// with one column of halo on each side, its row of b, and the rows j-1 and j+1
-// (columns c -/+ n).  These are 34 aligned 16-byte chunks, copied with one
-// cp.async per lane (two for lanes 0 and 1) into a ring of kFR levels in
-// shared memory; each lane keeps running pointers, so a level costs a handful
-// of instructions.  Columns whose neighbour across a face is not the adjacent
-// column of the staged rows (panel edges, periodic wrap) fetch it through the
-// neighbour table into a per-thread slot; only warps containing such a column
-// take that branch.  c'_k lives in shared memory as in k_smooth.
-// ---------------------------------------------------------------------------
-constexpr int kFR = 8;      // ring depth (levels)
-constexpr int kRowF = 136;  // floats per warp and slot: [own 40][b 32][j-1 32][j+1 32]
-constexpr int kOwnO = 0, kBO = 40, kJmO = 72, kJpO = 104;
-
-__host__ __device__ inline size_t rows_smem_bytes(int max_nz) {
-    return size_t(kBlk) * max_nz * 4 + size_t(kFR) * 4 * kRowF * 4 + size_t(kFR) * 2 * kBlk * 4 +
-           size_t(2 * max_nz + 1) * 4;
-}
-
 __device__ __forceinline__ void cp_async16(float *smem, const float *gmem, int nbytes) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes)
@@ -343,227 +319,6 @@ __device__ __forceinline__ void cp_async_wait_upto(int n) {
     }
 }
 
-template <int ZERO>
-__global__ void __launch_bounds__(kBlk) k_smooth_rows(const Lv<float> *__restrict__ L,
-                                                      const Item *__restrict__ items, float rho,
-                                                      int max_nz) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *cps = reinterpret_cast<float *>(smem_raw);  // c'[k][thread]
-    float *ring = cps + kBlk * max_nz;
-    float *fbr = ring + kFR * 4 * kRowF;
-    float *rad = fbr + kFR * 2 * kBlk;
-    const Item it = items[blockIdx.x];
-    const Lv<float> &d = L[it.lv];
-    const int nc = d.ncol, nz = d.nz, n = d.n;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c = it.col0 + tid;
-    const int c0w = it.col0 + 32 * warp;
-    const bool active = c < nc;
-    constexpr bool zero = ZERO == 1;
-    for (int i = tid; i < nz; i += kBlk) rad[i] = d.V[i];
-    for (int i = tid; i <= nz; i += kBlk) rad[nz + i] = d.g[i];
-    __syncthreads();
-    const float *Vs = rad, *gs = rad + nz;
-    const float *__restrict__ u = d.u[it.in];
-    float *__restrict__ un = d.u[it.out];
-    const float *__restrict__ b = d.b;
-    const size_t snc = size_t(nc);
-
-    // this lane's chunk copies: primary chunk q = lane, secondary q = 32 + lane (lanes 0, 1)
-    auto chunk = [&](int q, const float *&src, int &dst, int &nbytes) {
-        int scol;
-        bool use;
-        if (q < 10) {
-            src = u; scol = c0w - 4 + 4 * q; dst = kOwnO + 4 * q; use = !zero;
-        } else if (q < 18) {
-            src = b; scol = c0w + 4 * (q - 10); dst = kBO + 4 * (q - 10); use = true;
-        } else if (q < 26) {
-            src = u; scol = c0w - n + 4 * (q - 18); dst = kJmO + 4 * (q - 18); use = !zero;
-        } else {
-            src = u; scol = c0w + n + 4 * (q - 26); dst = kJpO + 4 * (q - 26); use = !zero;
-        }
-        use = use && scol >= 0 && scol + 4 <= nc;
-        src = use ? src + scol : b;  // an unused copy reads nothing (size 0)
-        nbytes = use ? 16 : 0;
-    };
-    const float *p1, *p2;
-    int dst1, dst2, nb1, nb2;
-    chunk(lane, p1, dst1, nb1);
-    chunk(32 + (lane & 1), p2, dst2, nb2);
-    const bool two = lane < 2;
-    if (!two) nb2 = 0;
-    const int adv1 = nb1 ? nc : 0, adv2 = nb2 ? nc : 0;
-
-    // stencil constants and the (at most two) neighbours outside the staged rows
-    Column<float> col;
-    col.A = 1.f; col.t0 = col.t1 = col.t2 = col.t3 = 0.f; col.s = 1.f;
-    col.nb = make_int4(0, 0, 0, 0);
-    int fd0 = -1, fd1 = -1;
-    const float *pf0 = u, *pf1 = u;
-    if (active) {
-        col = load_column(d, c);
-        const int want[4] = {c - 1, c + 1, c - n, c + n};
-        const int have[4] = {col.nb.x, col.nb.y, col.nb.z, col.nb.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (have[q] != want[q]) {
-                if (fd0 < 0) {
-                    fd0 = q;
-                    pf0 = u + have[q];
-                } else if (fd1 < 0) {
-                    fd1 = q;
-                    pf1 = u + have[q];
-                }
-            }
-    }
-    const bool warp_fb = !zero && __any_sync(0xffffffffu, fd0 >= 0);
-    const int nbf0 = fd0 >= 0 ? 4 : 0, nbf1 = fd1 >= 0 ? 4 : 0;
-    float *wring = ring + warp * kRowF;
-    float *s1 = wring + dst1, *s2 = wring + dst2;
-    float *f0s = fbr + tid, *f1s = fbr + kBlk + tid;
-
-    // copy level (next issue) into ring slot `slot` and advance the pointers
-    auto issue = [&](int slot) {
-        cp_async16(s1 + slot * 4 * kRowF, p1, nb1);
-        p1 += adv1;
-        if (two) {
-            cp_async16(s2 + slot * 4 * kRowF, p2, nb2);
-            p2 += adv2;
-        }
-        if (warp_fb) {
-            cp_async(f0s + slot * 2 * kBlk, pf0, nbf0 != 0);
-            cp_async(f1s + slot * 2 * kBlk, pf1, nbf1 != 0);
-            pf0 += snc;
-            pf1 += snc;
-        }
-        cp_async_commit();
-    };
-
-#pragma unroll
-    for (int j = 0; j < kFR - 1; ++j) issue(j);
-    float u0 = 0.f, um = 0.f;
-    if (!zero) {
-        cp_async_wait<kFR - 2>();
-        __syncwarp();
-        u0 = wring[kOwnO + 4 + lane];
-    }
-    float ratio = 0.f, fp = 0.f, gk = gs[0];
-    float *fpo = un + c;
-    float *cpw = cps + tid;
-    const int nblk = nz / kFR;
-#pragma unroll 1
-    for (int kb = 0; kb < nblk; ++kb) {
-        const bool last = kb == nblk - 1;
-#pragma unroll
-        for (int j = 0; j < kFR; ++j) {
-            const int k = kb * kFR + j;
-            __syncwarp();
-            if (!last) {
-                issue((j + kFR - 1) & (kFR - 1));
-                cp_async_wait<kFR - 2>();
-            } else {
-                if (j == 0) issue(kFR - 1);
-                cp_async_wait_upto(kFR - 2 - j);
-            }
-            __syncwarp();
-            const float *sk = wring + j * 4 * kRowF;
-            float r = sk[kBO + lane];
-            const float gk1 = gs[k + 1], Vk = Vs[k];
-            if (!zero) {
-                const float up = (last && j == kFR - 1) ? 0.f
-                                                        : wring[((j + 1) & (kFR - 1)) * 4 * kRowF +
-                                                                kOwnO + 4 + lane];
-                float nw = sk[kOwnO + 3 + lane], ne = sk[kOwnO + 5 + lane];
-                float ns = sk[kJmO + lane], nn = sk[kJpO + lane];
-                if (warp_fb) {
-                    const float v0 = f0s[j * 2 * kBlk], v1 = f1s[j * 2 * kBlk];
-                    nw = fd0 == 0 ? v0 : (fd1 == 0 ? v1 : nw);
-                    ne = fd0 == 1 ? v0 : (fd1 == 1 ? v1 : ne);
-                    ns = fd0 == 2 ? v0 : (fd1 == 2 ? v1 : ns);
-                    nn = fd0 == 3 ? v0 : (fd1 == 3 ? v1 : nn);
-                }
-                const float horiz = (col.t0 * (u0 - nw) + col.t1 * (u0 - ne)) +
-                                    (col.t2 * (u0 - ns) + col.t3 * (u0 - nn));
-                const float vert = gk1 * (u0 - up) + gk * (u0 - um);
-                r -= col.A * (Vk * u0) + Vk * horiz + col.A * vert;
-                um = u0;
-                u0 = up;
-            }
-            const float lo = col.A * gk, hi = col.A * gk1;
-            const float eps = Vk * col.s + lo * ratio;
-            const float inv = rcp(eps + hi);
-            fp = (r + lo * fp) * inv;
-            cpw[k * kBlk] = hi * inv;
-            if (active) fpo[size_t(k) * snc] = fp;
-            ratio = eps * inv;
-            gk = gk1;
-        }
-    }
-    __threadfence_block();  // the f'_k stores of this warp are seen by its copies below
-    __syncwarp();
-
-    // back substitution: slot fields [own 0..31] = f'_k, [b 0..31] = u_k
-    const bool bf = lane < 8, bu = !zero && lane >= 8 && lane < 16;
-    const int bcol = c0w + 4 * (lane & 7);
-    const int nbb = ((bf || bu) && bcol + 4 <= nc) ? 16 : 0;
-    const float *pb = nbb ? (bf ? un : u) + size_t(nz - 1) * snc + bcol : b;
-    const int advb = nbb ? nc : 0;
-    float *sb = wring + (bf ? kOwnO : kBO) + 4 * (lane & 7);
-    auto issue_back = [&](int slot) {
-        cp_async16(sb + slot * 4 * kRowF, pb, nbb);
-        pb -= advb;
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int j = 0; j < kFR - 1; ++j) issue_back(j);
-    float x = 0.f;
-#pragma unroll 1
-    for (int kb = 0; kb < nblk; ++kb) {
-        const bool last = kb == nblk - 1;
-#pragma unroll
-        for (int j = 0; j < kFR; ++j) {
-            const int jj = kb * kFR + j;  // levels from the top
-            const int k = nz - 1 - jj;
-            __syncwarp();
-            if (!last) {
-                issue_back((j + kFR - 1) & (kFR - 1));
-                cp_async_wait<kFR - 1>();  // level jj has landed
-            } else {
-                if (j == 0) issue_back(kFR - 1);
-                cp_async_wait_upto(kFR - 1 - j);
-            }
-            __syncwarp();
-            const float *sk = wring + j * 4 * kRowF;
-            const float fk = sk[kOwnO + lane];
-            const float uo = zero ? 0.f : sk[kBO + lane];
-            x = fk + cpw[k * kBlk] * x;
-            if (active) __stcs(un + size_t(k) * snc + c, uo + rho * x);
-        }
-    }
-    cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
-// Line smoother, two columns per thread (FP32, same eligibility as
-// k_smooth_rows).  Each thread of a 64-thread CTA sweeps the adjacent columns
-// c0 = col0 + 2t and c0 + 1 together with Blackwell's packed FP32x2
-// arithmetic (one instruction updates both columns), 64-bit shared-memory
-// loads, and one pipeline step per level for both.  A warp stages per level its
-// 64-column own row with one halo column each side, its rows of b, j-1 and j+1
-// (66 aligned 16-byte chunks) into a kFR-level ring.  The pivot recurrence is
-// recomputed in the back substitution from a checkpoint per kFR-level block
-// (identical instructions, so identical values), which keeps the shared memory
-// per CTA small; the number of resident CTAs is a tuning parameter (it bounds
-// the L2 working set of f' and u that the back substitution re-reads).
-// ---------------------------------------------------------------------------
-constexpr int kT2 = 64;                    // threads per CTA (2 columns each)
-constexpr int kRowF2 = 264;                // floats per warp and slot: [own 72][b 64][j-1 64][j+1 64]
-constexpr int kOwn2 = 0, kB2 = 72, kJm2 = 136, kJp2 = 200;
-
-__host__ __device__ inline size_t rows2_smem_bytes(int max_nz) {
-    return size_t(kFR) * 2 * kRowF2 * 4 + size_t(kFR) * 4 * kT2 * 4 +
-           size_t(max_nz / kFR) * kT2 * 8 + size_t(2 * max_nz + 1) * 4;
-}
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
@@ -584,246 +339,6 @@ __device__ __forceinline__ Piv2 pivot2(float2 Vs, float2 lo, float2 hi, float2 r
     return o;
 }
 
-template <int ZERO>
-__global__ void __launch_bounds__(kT2) k_smooth_rows2(const Lv<float> *__restrict__ L,
-                                                      const Item *__restrict__ items, float rho,
-                                                      int max_nz) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *ring = reinterpret_cast<float *>(smem_raw);
-    float *fbr = ring + kFR * 2 * kRowF2;
-    float2 *cpt = reinterpret_cast<float2 *>(fbr + kFR * 4 * kT2);
-    float *rad = reinterpret_cast<float *>(cpt + (max_nz / kFR) * kT2);
-    const Item it = items[blockIdx.x];
-    const Lv<float> &d = L[it.lv];
-    const int nc = d.ncol, nz = d.nz, n = d.n;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c0 = it.col0 + 2 * tid;  // this thread's columns c0, c0 + 1
-    const int c0w = it.col0 + 64 * warp;
-    const bool active = c0 < nc;       // ncol % 4 == 0: the pair is whole
-    constexpr bool zero = ZERO == 1;
-    for (int i = tid; i < nz; i += kT2) rad[i] = d.V[i];
-    for (int i = tid; i <= nz; i += kT2) rad[nz + i] = d.g[i];
-    __syncthreads();
-    const float *Vs = rad, *gs = rad + nz;
-    const float *__restrict__ u = d.u[it.in];
-    float *__restrict__ un = d.u[it.out];
-    const float *__restrict__ b = d.b;
-    const size_t snc = size_t(nc);
-
-    // chunk q of the warp's staged rows: source pointer (level 0), slot offset, size
-    auto chunk = [&](int q, const float *&src, int &dst, int &nbytes) {
-        int scol;
-        bool use;
-        if (q < 18) {
-            src = u; scol = c0w - 4 + 4 * q; dst = kOwn2 + 4 * q; use = !zero;
-        } else if (q < 34) {
-            src = b; scol = c0w + 4 * (q - 18); dst = kB2 + 4 * (q - 18); use = true;
-        } else if (q < 50) {
-            src = u; scol = c0w - n + 4 * (q - 34); dst = kJm2 + 4 * (q - 34); use = !zero;
-        } else {
-            src = u; scol = c0w + n + 4 * (q - 50); dst = kJp2 + 4 * (q - 50); use = !zero;
-        }
-        use = use && q < 66 && scol >= 0 && scol + 4 <= nc;
-        src = use ? src + scol : b;
-        nbytes = use ? 16 : 0;
-    };
-    const float *pa, *pb, *pc;
-    int da, db, dc, na, nb, ncb;
-    chunk(lane, pa, da, na);
-    chunk(lane + 32, pb, db, nb);
-    chunk(lane + 64, pc, dc, ncb);
-    const bool three = lane < 2;
-    const int adva = na ? nc : 0, advb = nb ? nc : 0, advc = ncb ? nc : 0;
-
-    // stencil constants of the two columns
-    float2 A = f2(1.f), t0 = f2(0.f), t1 = f2(0.f), t2 = f2(0.f), t3 = f2(0.f), sv = f2(1.f);
-    int4 nb0 = make_int4(0, 0, 0, 0), nb1 = nb0;
-    if (active) {
-        const Column<float> k0 = load_column(d, c0), k1 = load_column(d, c0 + 1);
-        A = make_float2(k0.A, k1.A);
-        t0 = make_float2(k0.t0, k1.t0);
-        t1 = make_float2(k0.t1, k1.t1);
-        t2 = make_float2(k0.t2, k1.t2);
-        t3 = make_float2(k0.t3, k1.t3);
-        sv = make_float2(k0.s, k1.s);
-        nb0 = k0.nb;
-        nb1 = k1.nb;
-    }
-    // Neighbours outside the staged rows (panel edges, periodic wrap).  For an
-    // even/odd column pair (n % 4 == 0) these are at most: the west neighbour
-    // of c0 or the east one of c0+1 (slot 0), and one of south/north for each
-    // column (slots 1, 2).  hd: 0 west of c0, 1 east of c0+1; vd0, vd1: 2 south,
-    // 3 north; -1 none.
-    int hd = -1, vd0 = -1, vd1 = -1, hc = 0, vc0 = 0, vc1 = 0;
-    if (active && !zero) {
-        if (nb0.x != c0 - 1) { hd = 0; hc = nb0.x; }
-        if (nb1.y != c0 + 2) { hd = 1; hc = nb1.y; }
-        if (nb0.z != c0 - n) { vd0 = 2; vc0 = nb0.z; }
-        if (nb0.w != c0 + n) { vd0 = 3; vc0 = nb0.w; }
-        if (nb1.z != c0 + 1 - n) { vd1 = 2; vc1 = nb1.z; }
-        if (nb1.w != c0 + 1 + n) { vd1 = 3; vc1 = nb1.w; }
-    }
-    const bool warp_fb = !zero && __any_sync(0xffffffffu, hd >= 0 || vd0 >= 0 || vd1 >= 0);
-    const float *pf0 = u + hc, *pf1 = u + vc0, *pf2 = u + vc1;
-    const bool f0 = hd >= 0, f1 = vd0 >= 0, f2b = vd1 >= 0;
-    float *wring = ring + warp * kRowF2;
-    float *sa = wring + da, *sb2 = wring + db, *sc = wring + dc;
-    float *fbt = fbr + tid;
-
-    auto issue = [&](int slot) {
-        const int so = slot * 2 * kRowF2;
-        cp_async16(sa + so, pa, na);
-        pa += adva;
-        cp_async16(sb2 + so, pb, nb);
-        pb += advb;
-        if (three) {
-            cp_async16(sc + so, pc, ncb);
-            pc += advc;
-        }
-        if (warp_fb) {
-            cp_async(fbt + (slot * 4 + 0) * kT2, pf0, f0);
-            cp_async(fbt + (slot * 4 + 1) * kT2, pf1, f1);
-            cp_async(fbt + (slot * 4 + 2) * kT2, pf2, f2b);
-            pf0 += snc;
-            pf1 += snc;
-            pf2 += snc;
-        }
-        cp_async_commit();
-    };
-
-#pragma unroll
-    for (int j = 0; j < kFR - 1; ++j) issue(j);
-    const int own = kOwn2 + 4 + 2 * lane;  // this thread's pair in the own row
-    float2 u0 = f2(0.f), um = f2(0.f);
-    if (!zero) {
-        cp_async_wait<kFR - 2>();
-        __syncwarp();
-        u0 = *reinterpret_cast<const float2 *>(wring + own);
-    }
-    float2 ratio = f2(0.f), fp = f2(0.f);
-    float gk = gs[0];
-    float2 *fpo = reinterpret_cast<float2 *>(un + c0);
-    const int nblk = nz / kFR;
-#pragma unroll 1
-    for (int kb = 0; kb < nblk; ++kb) {
-        const bool last = kb == nblk - 1;
-        if (active) cpt[kb * kT2 + tid] = ratio;
-#pragma unroll
-        for (int j = 0; j < kFR; ++j) {
-            const int k = kb * kFR + j;
-            __syncwarp();
-            if (!last) {
-                issue((j + kFR - 1) & (kFR - 1));
-                cp_async_wait<kFR - 2>();
-            } else {
-                if (j == 0) issue(kFR - 1);
-                cp_async_wait_upto(kFR - 2 - j);
-            }
-            __syncwarp();
-            const float *sk = wring + j * 2 * kRowF2;
-            float2 r = *reinterpret_cast<const float2 *>(sk + kB2 + 2 * lane);
-            const float gk1 = gs[k + 1], Vk = Vs[k];
-            if (!zero) {
-                const float2 up = (last && j == kFR - 1)
-                                      ? f2(0.f)
-                                      : *reinterpret_cast<const float2 *>(
-                                            wring + ((j + 1) & (kFR - 1)) * 2 * kRowF2 + own);
-                float2 nw = make_float2(sk[own - 1], u0.x);
-                float2 ne = make_float2(u0.y, sk[own + 2]);
-                float2 ns = *reinterpret_cast<const float2 *>(sk + kJm2 + 2 * lane);
-                float2 nn = *reinterpret_cast<const float2 *>(sk + kJp2 + 2 * lane);
-                if (warp_fb) {
-                    const float v0 = fbt[(j * 4 + 0) * kT2], v1 = fbt[(j * 4 + 1) * kT2];
-                    const float v2 = fbt[(j * 4 + 2) * kT2];
-                    nw.x = hd == 0 ? v0 : nw.x;
-                    ne.y = hd == 1 ? v0 : ne.y;
-                    ns.x = vd0 == 2 ? v1 : ns.x;
-                    nn.x = vd0 == 3 ? v1 : nn.x;
-                    ns.y = vd1 == 2 ? v2 : ns.y;
-                    nn.y = vd1 == 3 ? v2 : nn.y;
-                }
-                float2 horiz = __fmul2_rn(t0, sub2(u0, nw));
-                horiz = __ffma2_rn(t1, sub2(u0, ne), horiz);
-                horiz = __ffma2_rn(t2, sub2(u0, ns), horiz);
-                horiz = __ffma2_rn(t3, sub2(u0, nn), horiz);
-                float2 vert = __fmul2_rn(f2(gk1), sub2(u0, up));
-                vert = __ffma2_rn(f2(gk), sub2(u0, um), vert);
-                float2 Au = __fmul2_rn(A, __fmul2_rn(f2(Vk), u0));
-                Au = __ffma2_rn(f2(Vk), horiz, Au);
-                Au = __ffma2_rn(A, vert, Au);
-                r = sub2(r, Au);
-                um = u0;
-                u0 = up;
-            }
-            const float2 lo = __fmul2_rn(A, f2(gk)), hi = __fmul2_rn(A, f2(gk1));
-            const Piv2 pv = pivot2(__fmul2_rn(f2(Vk), sv), lo, hi, ratio);
-            fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
-            if (active) fpo[size_t(k) * (snc / 2)] = fp;
-            ratio = pv.ratio_next;
-            gk = gk1;
-        }
-    }
-    __threadfence_block();  // the f'_k stores of this warp are seen by its copies below
-    __syncwarp();
-
-    // back substitution: slot fields [own 0..63] = f'_k, [b 0..63] = u_k (64 floats each)
-    const bool bf = lane < 16, bu = !zero && lane >= 16;
-    const int bcol = c0w + 4 * (lane & 15);
-    const int nbb = bcol + 4 <= nc ? 16 : 0;
-    const float *pbk = nbb && (bf || bu) ? (bf ? un : u) + size_t(nz - 1) * snc + bcol : b;
-    const int nbk = (bf || bu) ? nbb : 0;
-    const int advk = nbk ? nc : 0;
-    float *sbk = wring + (bf ? kOwn2 : kB2) + 4 * (lane & 15);
-    auto issue_back = [&](int slot) {
-        cp_async16(sbk + slot * 2 * kRowF2, pbk, nbk);
-        pbk -= advk;
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int j = 0; j < kFR - 1; ++j) issue_back(j);
-    float2 x = f2(0.f);
-    float2 *uout = reinterpret_cast<float2 *>(un + c0);
-#pragma unroll 1
-    for (int kb = nblk - 1; kb >= 0; --kb) {
-        // recompute c'_k of the block from its checkpoint
-        float2 cpr[kFR];
-        {
-            float2 rt = active ? cpt[kb * kT2 + tid] : f2(0.f);
-            float g0 = gs[kb * kFR];
-#pragma unroll
-            for (int j = 0; j < kFR; ++j) {
-                const int k = kb * kFR + j;
-                const float g1 = gs[k + 1];
-                const float2 lo = __fmul2_rn(A, f2(g0)), hi = __fmul2_rn(A, f2(g1));
-                const Piv2 pv = pivot2(__fmul2_rn(f2(Vs[k]), sv), lo, hi, rt);
-                cpr[j] = pv.cp;
-                rt = pv.ratio_next;
-                g0 = g1;
-            }
-        }
-        const bool last = kb == 0;
-#pragma unroll
-        for (int jj = kFR - 1; jj >= 0; --jj) {
-            const int k = kb * kFR + jj;
-            const int step = kFR - 1 - jj;  // position within this block, top first
-            __syncwarp();
-            if (!last) {
-                issue_back((step + kFR - 1) & (kFR - 1));
-                cp_async_wait<kFR - 1>();
-            } else {
-                if (step == 0) issue_back(kFR - 1);
-                cp_async_wait_upto(kFR - 1 - step);
-            }
-            __syncwarp();
-            const float *sk = wring + step * 2 * kRowF2;
-            const float2 fk = *reinterpret_cast<const float2 *>(sk + kOwn2 + 2 * lane);
-            const float2 uo = zero ? f2(0.f) : *reinterpret_cast<const float2 *>(sk + kB2 + 2 * lane);
-            x = __ffma2_rn(cpr[jj], x, fk);
-            if (active) __stcs(uout + size_t(k) * (snc / 2), __ffma2_rn(f2(rho), x, uo));
-        }
-    }
-    cp_async_wait<0>();
-}
 
 // ---------------------------------------------------------------------------
 // Tensor memory (TMEM, 128 lanes x 512 32-bit columns per SM) as per-thread
@@ -2279,10 +1794,6 @@ bool smooth_uses_global_scratch(int max_nz, size_t elem_bytes) {
     return !(elem_bytes == 4 && cpb + ring <= kSmemCap);
 }
 
-bool smooth_rows_fits(int max_nz) {
-    return rows_smem_bytes(max_nz) <= kSmemCap && rows2_smem_bytes(max_nz) <= kSmemCap;
-}
-
 template <typename T, int Z>
 static cudaError_t launch_smooth_z(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
                                    T rho, int max_nz) {
@@ -2298,42 +1809,6 @@ static cudaError_t launch_smooth_z(cudaStream_t s, const Lv<T> *L, const Item *i
         k_smooth<T, false, Z><<<nitems, kBlk, ring, s>>>(L, items, rho, 0);
     }
     return cudaGetLastError();
-}
-
-template <int Z>
-static cudaError_t launch_rows_z(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
-                                 float rho, int max_nz, int ctas_per_sm) {
-    size_t bytes = rows_smem_bytes(max_nz);
-    // pad the request to cap the CTAs per SM (bounds the L2 working set)
-    if (ctas_per_sm > 0) {
-        const size_t cap = (size_t(228) * 1024) / size_t(ctas_per_sm) - 1024;
-        if (cap > bytes) bytes = cap;
-    }
-    cudaError_t e = set_smem(k_smooth_rows<Z>, bytes);
-    if (e != cudaSuccess) return e;
-    k_smooth_rows<Z><<<nitems, kBlk, bytes, s>>>(L, items, rho, max_nz);
-    return cudaGetLastError();
-}
-
-template <int Z>
-static cudaError_t launch_rows2_z(cudaStream_t s, const Lv<float> *L, const Item *items,
-                                  int nitems, float rho, int max_nz, int ctas_per_sm) {
-    size_t bytes = rows2_smem_bytes(max_nz);
-    if (ctas_per_sm > 0) {
-        const size_t cap = (size_t(228) * 1024) / size_t(ctas_per_sm) - 1024;
-        if (cap > bytes) bytes = cap;
-    }
-    cudaError_t e = set_smem(k_smooth_rows2<Z>, bytes);
-    if (e != cudaSuccess) return e;
-    k_smooth_rows2<Z><<<nitems, kT2, bytes, s>>>(L, items, rho, max_nz);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_smooth_rows2(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
-                                float rho, int max_nz, int zero_mode, int ctas_per_sm) {
-    if (nitems <= 0) return cudaSuccess;
-    if (zero_mode == 1) return launch_rows2_z<1>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
-    return launch_rows2_z<0>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
 
 template <int Z, int FR, bool ALN, bool TM>
@@ -2393,13 +1868,6 @@ cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *ite
 bool smooth_tw_fits(int max_nz, int ring) {
     return max_nz % 2 == 0 && (max_nz / 2) % ring == 0 &&
            tw_smem_bytes(max_nz, ring, false) <= kSmemCap;
-}
-
-cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
-                               float rho, int max_nz, int zero_mode, int ctas_per_sm) {
-    if (nitems <= 0) return cudaSuccess;
-    if (zero_mode == 1) return launch_rows_z<1>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
-    return launch_rows_z<0>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
 
 template <typename T>

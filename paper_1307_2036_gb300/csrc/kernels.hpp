@@ -15,25 +15,20 @@ template <typename T>
 cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems, T rho,
                           int max_nz, int zero_mode);
 
-// Row-staged FP32 smoother: valid when every item's level has n % 4 == 0,
-// ncol % 4 == 0 and nz % 8 == 0 and zero_mode is 0 or 1.  ctas_per_sm > 0
-// caps the resident CTAs per SM (through the shared-memory request).
-cudaError_t launch_smooth_rows(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
-                               float rho, int max_nz, int zero_mode, int ctas_per_sm);
-// Same sweep with two columns per thread and packed FP32x2 arithmetic (64-thread CTAs
-// over the same 128-column items).
+// Twisted FP32 line smoother (one column per thread, row-staged cp.async
+// ring; see k_smooth_tw): valid when every item's level has n % 4 == 0,
+// ncol % 4 == 0, an even nz with (nz/2) % ring == 0, and zero_mode 0 or 1.
+// ctas_per_sm > 0 caps the resident CTAs per SM (through the shared-memory
+// request); ring is the staging depth (4 or 8 steps); aligned: every level has
+// n % 32 == 0.
 cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                              float rho, int max_nz, int zero_mode, int ctas_per_sm, int ring,
                              bool aligned);
 bool smooth_tw_fits(int max_nz, int ring);
-cudaError_t launch_smooth_rows2(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
-                                float rho, int max_nz, int zero_mode, int ctas_per_sm);
 
 // Whether the generic smoother keeps its Thomas coefficients in the level's
-// aux buffer (true) or in shared memory, and whether the row-staged kernel's
-// shared memory fits, for a largest nz of max_nz.
+// aux buffer (true) or in shared memory, for a largest nz of max_nz.
 bool smooth_uses_global_scratch(int max_nz, size_t elem_bytes);
-bool smooth_rows_fits(int max_nz);
 
 // mode 0: aux = A u[in]; mode 1: aux = b - A u[in]; mode 2: only the partial
 // sums of (b - A u[in])^2 into partials[item] (FP64).

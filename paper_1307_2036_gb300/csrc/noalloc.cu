@@ -1,14 +1,16 @@
 // Line smoothing without any device allocation.
 //
 // ellsolve_level_smooth allocates a partner buffer and Thomas scratch with
-// cudaMalloc on every call.  Some callers cannot do that: code that runs while
-// a CUDA stream is being captured into a graph (an allocation there is either
-// refused or breaks the capture), callers that hand the library a fixed memory
-// budget owned by their own allocator or memory pool, and latency-critical
-// loops where a cudaMalloc may synchronise the device or fragment memory.
+// cudaMalloc on every call.  Some callers cannot do that: a host program that
+// hands the library a fixed device-memory budget owned by its own allocator or
+// memory pool (a cudaMalloc behind the pool's back would overrun the budget or
+// fail once the pool holds the memory), and latency-critical loops where a
+// cudaMalloc / cudaFree pair may synchronise the device or fragment memory.
 // ellsolve_level_smooth_noalloc runs the same kernels with all of its scratch
 // -- the level descriptor, the work items, the partner iterate and the Thomas
 // scratch -- carved out of one file-scope device array of kStaticScratchBytes.
+// It copies the descriptor and items from host memory and waits for its
+// stream before returning, so it is an ordinary blocking call.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -52,6 +54,13 @@ template <typename T>
 ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int nsweeps,
                               double rho) {
     if (level < 0 || level >= p.nlev) throw Error(ELLSOLVE_ERR_ARG, "level out of range");
+    // the scratch array is per device: the handle's buffers and stream live on
+    // the device current at its creation, so the same device must be current
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != p.device)
+        throw Error(ELLSOLVE_ERR_ARG, "current device " + std::to_string(dev) +
+                                          " is not the handle's device " + std::to_string(p.device));
     if (sizeof(T) == 8 && level > 0 && p.opts.precision != 0)
         throw Error(ELLSOLVE_ERR_ARG, "FP64 coarse levels exist only with precision 0");
     if (sizeof(T) == 4 && p.opts.precision != 1)

@@ -196,6 +196,7 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
     grid = g;
     opts = o;
     stream = s;
+    check_cuda(cudaGetDevice(&device), "cudaGetDevice");
     nz = g.nz;
     geom = geometry_for(g, o.coarsest_min, o.max_levels, s);
     P = geom->P;
@@ -654,12 +655,12 @@ bool restrict_rows_preferred(const Problem &p, int level) {
     return restrict_rows_eligible(p, level) && p.lev[level + 1].ncol >= 4 * 152 * kBlk;
 }
 
+// Levels the twisted FP32 smoother takes (every other level and the FP64
+// path take the generic kernel).
 bool rows_eligible(const Problem &p, int level) {
     const LevelStore &Ls = p.lev[level];
     if (Ls.n % 4 != 0 || Ls.ncol % 4 != 0) return false;
-    if (p.smooth_variant == 3) return p.nz % 16 == 0 && smooth_tw_fits(p.nz, 8);
-    // the one-sided row kernels have no red-black half-sweeps
-    return p.opts.smoother == 0 && p.nz % 8 == 0 && smooth_rows_fits(p.nz);
+    return p.nz % 16 == 0 && smooth_tw_fits(p.nz, 8);
 }
 
 template <typename T>
@@ -667,18 +668,9 @@ void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Ite
                      double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned) {
     if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
         const Lv<float> *Lf = reinterpret_cast<const Lv<float> *>(L);
-        if (p.smooth_variant == 3)
-            check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode,
-                                        p.smooth_ctas_per_sm, p.smooth_ring, aligned),
-                       "smooth_tw");
-        else if (p.smooth_variant == 2)
-            check_cuda(launch_smooth_rows2(s, Lf, it, n, float(rho), max_nz, zero_mode,
-                                           p.smooth_ctas_per_sm),
-                       "smooth_rows2");
-        else
-            check_cuda(launch_smooth_rows(s, Lf, it, n, float(rho), max_nz, zero_mode,
-                                          p.smooth_ctas_per_sm),
-                       "smooth_rows");
+        check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode,
+                                    p.smooth_ctas_per_sm, p.smooth_ring, aligned),
+                   "smooth_tw");
     } else {
         check_cuda(launch_smooth<T>(s, L, it, n, T(rho), max_nz, zero_mode), "smooth");
     }
@@ -1738,11 +1730,8 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
     check_cuda(cudaEventCreate(&e0), "event");
     check_cuda(cudaEventCreate(&e1), "event");
     // (resident CTAs per SM, ring depth) candidates of the smoother in use
-    std::vector<std::pair<int, int>> candidates;
-    if (h->smooth_variant == 3)
-        candidates = {{3, 8}, {4, 8}, {5, 8}, {3, 4}, {4, 4}, {5, 4}};
-    else
-        candidates = {{2, 8}, {3, 8}, {4, 8}, {5, 8}, {6, 8}};
+    const std::vector<std::pair<int, int>> candidates = {{3, 8}, {4, 8}, {5, 8},
+                                                         {3, 4}, {4, 4}, {5, 4}};
     int best = h->smooth_ctas_per_sm, best_ring = h->smooth_ring;
     double best_ms = 1e300;
     const int keep = h->smooth_ctas_per_sm, keep_ring = h->smooth_ring;

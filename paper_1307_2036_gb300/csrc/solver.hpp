@@ -151,6 +151,7 @@ struct Problem {
     int nz = 0, P = 1, nlev = 0;
     size_t N = 0;
     cudaStream_t stream = nullptr;      // the caller's stream: all work is ordered on it
+    int device = 0;                     // the device current at creation (owns every buffer)
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     std::shared_ptr<const Geometry> geom;
     std::vector<LevelStore> lev;
@@ -166,10 +167,8 @@ struct Problem {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_graph;
     int ev_next = 0, ev_graph_used = 0;
-    int smooth_ctas_per_sm = 3;  // row-staged smoother occupancy cap (0: as many as fit)
+    int smooth_ctas_per_sm = 3;  // twisted smoother's occupancy cap (0: as many as fit)
     int smooth_ring = 8;         // twisted smoother's staging ring depth (4 or 8 steps)
-    int smooth_variant = 3;      // FP32 row-staged smoother: 3 twisted (one column/thread),
-                                 // 2 two columns/thread, 1 one column/thread
     double prof_ms = 0.0, prof_bytes = 0.0;
     long prof_count = 0;
     std::vector<double> ev_free_bytes, ev_graph_bytes;  // bytes per recorded pair

@@ -21,17 +21,24 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def sensitivity(fn, *arrays, trials=2, seed=0, ulps=4):
-    """Relative L2 change of fn's output when each input is perturbed by random
-    relative amounts of up to `ulps` machine epsilons: how far two correct FP64
-    evaluations of the same map can drift apart from rounding alone."""
-    eps = np.finfo(np.float64).eps
+def sensitivity(fn, *arrays, trials=2, seed=0, ulps=4, eps=None, norm="l2"):
+    """Relative change of fn's output when each input is perturbed by random
+    relative amounts of up to `ulps` units of `eps` (default the FP64 machine
+    epsilon): how far two correct evaluations of the same map at that
+    precision can drift apart from rounding alone.  norm "l2": relative L2
+    change; "max": largest element change over the output's largest element."""
+    eps = np.finfo(np.float64).eps if eps is None else eps
     base = fn(*arrays)
     rng = np.random.default_rng(seed)
     worst = 0.0
     for _ in range(trials):
         pert = [a * (1.0 + ulps * eps * rng.uniform(-1.0, 1.0, np.shape(a))) for a in arrays]
-        worst = max(worst, rel_l2(fn(*pert), base))
+        out = fn(*pert)
+        if norm == "max":
+            d = np.max(np.abs(out - base)) / max(np.max(np.abs(base)), 1e-300)
+        else:
+            d = rel_l2(out, base)
+        worst = max(worst, d)
     return worst
 
 
@@ -39,6 +46,18 @@ def fp64_tol(fn, *arrays, floor=1e-13):
     """Tolerance of an FP64 parity check: 16x the oracle's own rounding
     sensitivity, at least `floor`."""
     return max(floor, 16.0 * sensitivity(fn, *arrays))
+
+
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+def fp32_tol(fn, *arrays, floor=1e-6, norm="l2"):
+    """Tolerance of an FP32 parity check against the FP64 oracle: 16x the
+    oracle's sensitivity to binary32-level (4 eps32) relative changes of its
+    inputs, at least `floor`.  The sensitivity is an empirical condition
+    estimate of the map at FP32 precision: one sweep's rounding of the
+    residual is of that size, and the tridiagonal solve amplifies both alike."""
+    return max(floor, 16.0 * sensitivity(fn, *arrays, eps=EPS32, norm=norm))
 
 
 class Pair:

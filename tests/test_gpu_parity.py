@@ -277,6 +277,30 @@ def test_batch_equals_alone(torch_mod, oracle_mod):
         assert rb.rel_residual <= 1e-8
 
 
+def test_batch_matches_the_oracle(torch_mod, oracle_mod):
+    """Each member of a batched mixed-precision solve (mixed grids, sizes and
+    parameters) against the oracle's converged FP64 multigrid solution of its
+    own problem: relative L2 <= 1e-9."""
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    specs = [(1, 8, 16, 0.01, 1.0), (0, 24, 12, 0.05, 4.0), (1, 12, 8, 0.002, 0.5),
+             (1, 32, 32, 0.01, 1.0), (0, 64, 16, 0.02, 2.0)]
+    solvers, rhs, xs = [], [], []
+    for m, (kind, n, nz, w2, l2) in enumerate(specs):
+        s = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=True), w2, l2, precision=1)
+        solvers.append(s)
+        rhs.append(torch.tensor(inputs.uniform_pm1(s.shape(), member=20 + m), device="cuda"))
+        xs.append(torch.zeros_like(rhs[-1]))
+    st, res = ellsolve.solve_batch(solvers, rhs, xs, rtol=1e-12, maxit=80)
+    torch.cuda.synchronize()
+    for (kind, n, nz, w2, l2), f, x, r in zip(specs, rhs, xs, res):
+        og = oracle_mod.Grid(kind, n, nz, inputs.radial_levels(nz, graded=True), w2, l2)
+        u, _, _ = og.mg_solve(og.volumes() * f.cpu().numpy(), rtol=1e-13, maxit=200)
+        err = rel_l2(x.cpu().numpy(), u)
+        print(f"batch member {(kind, n, nz)}: {r.iterations} V-cycles, error {err:.2e}")
+        assert err <= 1e-9
+
+
 def test_autotune_changes_no_result(torch_mod, oracle_mod):
     """ellsolve_autotune only changes the smoother's occupancy cap: a solve
     before and after tuning gives the same bits."""

@@ -122,3 +122,39 @@ def test_nonfinite_rhs_reported(torch_mod):
     assert st_b == ellsolve.ERR_NONFINITE
     assert st_g == ellsolve.OK and res_g.rel_residual <= 1e-8
     srv.close()
+
+
+def _oracle_solution(oracle_mod, spec, f_host):
+    kind, n, nz, graded, w2, l2, _ = spec
+    og = oracle_mod.Grid(kind, n, nz, inputs.radial_levels(nz, graded=graded), w2, l2)
+    b = og.volumes() * f_host
+    u, _, hist = og.mg_solve(b, rtol=1e-13, maxit=200)
+    return og, b, u
+
+
+@pytest.mark.parametrize("slots", [3])
+def test_served_results_match_the_oracle(torch_mod, oracle_mod, slots):
+    """Every served result against the FP64 oracle: requests at rtol 1e-12
+    (mixed precision) match the oracle's converged multigrid solution to
+    relative L2 1e-9, and the residual each request reports is the oracle's
+    residual of the returned x to 1%."""
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    fs = [rhs(torch, s[0], s[1], s[2], 60 + i) for i, s in enumerate(SPECS)]
+    srv = ellsolve.Server(hbm_budget_bytes=4 << 30, max_slots=slots)
+    xs = [torch.zeros_like(f) for f in fs]
+    torch.cuda.synchronize()
+    tickets = [srv.submit(s[0], s[1], s[2], inputs.radial_levels(s[2], graded=s[3]), s[4], s[5],
+                          f, x, rtol=1e-12, maxit=80) for s, f, x in zip(SPECS, fs, xs)]
+    for spec, t, f, x in zip(SPECS, tickets, fs, xs):
+        st, res = srv.poll(t, timeout_us=-1)
+        assert st in (ellsolve.OK, ellsolve.NOT_CONVERGED), st
+        og, b, u = _oracle_solution(oracle_mod, spec, f.cpu().numpy())
+        xh = x.cpu().numpy()
+        err = np.linalg.norm(xh - u) / np.linalg.norm(u)
+        rel = np.linalg.norm(og.residual(b, xh)) / np.linalg.norm(b)
+        print(f"served {spec[:3]}: status {st}, {res.iterations} V-cycles, error {err:.2e}, "
+              f"reported residual {res.rel_residual:.2e}, oracle residual {rel:.2e}")
+        assert err <= 1e-9
+        assert abs(rel - res.rel_residual) <= 1e-2 * rel + 1e-16
+    srv.close()
