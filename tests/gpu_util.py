@@ -51,15 +51,6 @@ def fp64_tol(fn, *arrays, floor=1e-13):
 EPS32 = float(np.finfo(np.float32).eps)
 
 
-def fp32_tol(fn, *arrays, floor=1e-6, norm="l2"):
-    """Tolerance of an FP32 parity check against the FP64 oracle: 16x the
-    oracle's sensitivity to binary32-level (4 eps32) relative changes of its
-    inputs, at least `floor`.  The sensitivity is an empirical condition
-    estimate of the map at FP32 precision: one sweep's rounding of the
-    residual is of that size, and the tridiagonal solve amplifies both alike."""
-    return max(floor, 16.0 * sensitivity(fn, *arrays, eps=EPS32, norm=norm))
-
-
 class Pair:
     """An oracle grid and a library solver for the same problem."""
 

@@ -1,20 +1,30 @@
 """FP32 line smoother on fully random iterates at n_z = 128, on the launches that
 park the eliminated right-hand side in tensor memory (at least 152 blocks of
-128 columns), against the FP64 oracle element by element.
+128 columns), against the definition of a sweep (Sec. 4.2): u1 = u0 + rho d
+with Dtilde d = b - A u0, Dtilde the block (vertical tridiagonal) part of A.
 
-An FP32 sweep rounds the residual b - A u, whose terms are much larger than
-the residual itself on graded columns, and the tridiagonal solve amplifies that
-rounding by the column's condition.  The tolerance is therefore derived, not
-fixed: 16x the oracle's own response to binary32-level (4 eps32) relative
-changes of its inputs u and b (an empirical condition estimate at FP32
-precision), in the relative L2 norm and, element by element, relative to the
-largest element.  The achieved error and the tolerance are printed.
+The forward error of an FP32 sweep against the FP64 oracle is not a useful
+bar here: the sweep rounds b - A u0, whose vertical terms are up to ~1e10
+times the column's diagonal excess on graded columns, and Dtilde^{-1}
+amplifies that rounding by the same factor (observed forward errors 1e-2 at
+omega^2 = 0.01 and O(1) with strong coupling, while any correct FP32
+evaluation may differ from another that much).  What a correct FP32 sweep
+does guarantee is a small componentwise backward error: evaluated in FP64,
+    |Dtilde d - (b - A u0)| <= C eps32 (|b| + |A||u0| + |Dtilde||d| + |Dtilde||u1|/rho)
+(rounding of the residual's terms, of the elimination -- backward stable for
+these M-matrices -- of the FP32 coefficients, and of the final update).  The
+test checks it element by element with C = 32, for one sweep and for the
+second sweep from the first one's FP32 result, and prints the achieved
+backward error and the forward error.  A wrong level, neighbour, coefficient
+or colour gives an O(1) backward error.  The operator pieces are taken from
+the oracle's geometry (areas, transmissibilities, neighbours) and radial
+vectors; their sum is checked against the oracle's own A u first.
 """
 import numpy as np
 import pytest
 
 from paper_1307_2036_gb300 import inputs
-from gpu_util import Pair, fp32_tol, rel_l2, require_gpu
+from gpu_util import EPS32, Pair, rel_l2, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -26,6 +36,7 @@ CASES = [
     (0, 160, 128, True, 0.1, 25.0, 0),   # box, strong vertical coupling (ill-conditioned columns)
 ]
 IDS = ["sph64z128", "sph80z128", "sph64z128rb", "box160z128strong"]
+C_BACKWARD = 32.0
 
 
 @pytest.fixture(scope="module")
@@ -37,35 +48,93 @@ def f32exact(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
+class Pieces:
+    """Mass, horizontal and vertical parts of A on level 0 of an oracle grid,
+    as (nz, ncol) maps, with their absolute-value counterparts."""
+
+    def __init__(self, og):
+        self.og = og
+        area, trans, nbr = og.geometry()
+        V, G = og.radial()
+        w2, l2 = og.omega2, og.lambda2
+        self.nz, self.nc = og.nz, og.ncol()
+        self.mass = area[None, :] * V[:, None]                      # A_P V_k
+        self.tq = w2 * V[:, None, None] * trans[None, :, :]         # w2 V_k T_q  (nz, nc, 4)
+        self.nbr = nbr
+        self.gu = w2 * l2 * area[None, :] * G[1:, None]             # coupling to k+1
+        self.gd = w2 * l2 * area[None, :] * G[:-1, None]            # coupling to k-1
+
+    def _shift(self, x):
+        up = np.zeros_like(x)
+        dn = np.zeros_like(x)
+        up[:-1] = x[1:]
+        dn[1:] = x[:-1]
+        return up, dn
+
+    def diag_block(self, x, absolute=False):
+        """Dtilde x (or |Dtilde| |x|): mass, the diagonal of the horizontal part
+        and the vertical part."""
+        up, dn = self._shift(x)
+        hd = self.tq.sum(axis=2)
+        if absolute:
+            x, up, dn = np.abs(x), np.abs(up), np.abs(dn)
+            return (self.mass + hd) * x + self.gu * (x + up) + self.gd * (x + dn)
+        return (self.mass + hd) * x + self.gu * (x - up) + self.gd * (x - dn)
+
+    def apply(self, x, absolute=False):
+        """A x (or |A| |x|)."""
+        nb = x[:, self.nbr]                                          # (nz, nc, 4)
+        if absolute:
+            return self.diag_block(x, True) + (self.tq * np.abs(nb)).sum(axis=2)
+        return self.diag_block(x) - (self.tq * nb).sum(axis=2)
+
+
+def backward_error(pc, b, u0, u1, rho, cols=None):
+    """Largest componentwise backward error of the sweep u0 -> u1, over the
+    updated columns `cols` (all when None), in units of eps32."""
+    d = (u1 - u0) / rho
+    lhs = pc.diag_block(d) - (b - pc.apply(u0))
+    bound = (np.abs(b) + pc.apply(u0, True) + pc.diag_block(d, True) +
+             pc.diag_block(u1, True) / rho)
+    ratio = np.abs(lhs) / bound / EPS32
+    if cols is not None:
+        ratio = ratio[:, cols]
+    return float(ratio.max())
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_fp32_smoother_random_iterate(torch_mod, oracle_mod, case):
     kind, n, nz, graded, w2, l2, smoother = case
     p = Pair(oracle_mod, kind, n, nz, omega2=w2, lambda2=l2, graded=graded, precision=1,
              smoother=smoother)
-    ncol = p.og.ncol()
-    assert (ncol + 127) // 128 >= 152  # the tensor-memory launch
+    nc = p.og.ncol()
+    assert (nc + 127) // 128 >= 152  # the tensor-memory launch
+    pc = Pieces(p.og)
     sh = p.og.shape()
-    u = f32exact(inputs.uniform_pm1(sh, member=501))
-    b = f32exact(p.og.volumes() * inputs.uniform_pm1(sh, member=502))
+    u0 = f32exact(inputs.uniform_pm1(sh, member=501)).reshape(nz, nc)
+    b = f32exact(p.og.volumes() * inputs.uniform_pm1(sh, member=502)).reshape(nz, nc)
+    # the test's operator pieces are the oracle's operator
+    assert rel_l2(pc.apply(u0), p.og.apply(u0).reshape(nz, nc)) <= 1e-13
     rho = 1.0 if smoother == 1 else 0.8
-    fn = lambda bb, uu: p.og.smooth(bb, uu, 2, rho) if smoother == 0 else _rb(p, bb, uu, rho)
-    ref = fn(b, u)
-    tol_l2 = fp32_tol(fn, b, u)
-    tol_max = fp32_tol(fn, b, u, norm="max")
-    ud = p.dev(u, True)
-    p.sv.level_smooth(0, p.dev(b, True), ud, nsweeps=2, rho=rho, fp32=True)
-    got = p.host(ud)
-    err = rel_l2(got, ref)
-    emax = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
-    print(f"{n}x{n}x{nz} smoother {smoother}: L2 {err:.2e} (tol {tol_l2:.2e}), "
-          f"max {emax:.2e} (tol {tol_max:.2e})")
-    assert err <= tol_l2
-    assert emax <= tol_max
-
-
-def _rb(p, b, u, rho):
-    """Two block red-black SOR sweeps of the oracle (smoother 1)."""
-    og = p.og
-    from oracle import Grid
-    g = Grid(og.kind, og.n, og.nz, p.r, og.omega2, og.lambda2, smoother=1)
-    return g.smooth(b, u, 2, rho)
+    bd = p.dev(b.reshape(sh), True)
+    ud = p.dev(u0.reshape(sh), True)
+    iters = [u0]
+    for sweep in range(2):
+        p.sv.level_smooth(0, bd, ud, nsweeps=1, rho=rho, fp32=True)
+        iters.append(p.host(ud).reshape(nz, nc))
+    worst = 0.0
+    for s in range(2):
+        ua, ub = iters[s], iters[s + 1]
+        if smoother == 0:
+            worst = max(worst, backward_error(pc, b, ua, ub, rho))
+        else:
+            # red columns from ua, then black columns from the half-swept iterate
+            red = p.og.colour() == 0
+            mid = np.where(red[None, :], ub, ua)
+            worst = max(worst, backward_error(pc, b, ua, mid, rho, cols=red))
+            worst = max(worst, backward_error(pc, b, mid, ub, rho, cols=~red))
+    fwd_ref = (p.og.smooth(b.reshape(sh), u0.reshape(sh), 2, rho) if smoother == 0 else None)
+    fwd = rel_l2(iters[2], fwd_ref) if fwd_ref is not None else float("nan")
+    print(f"{n}x{n}x{nz} smoother {smoother}: componentwise backward error {worst:.2f} eps32 "
+          f"(bar {C_BACKWARD:.0f}), forward error of two sweeps against the oracle {fwd:.2e}")
+    assert worst <= C_BACKWARD
