@@ -408,10 +408,9 @@ __device__ __forceinline__ void tm_ld<8>(unsigned taddr, unsigned (&v)[16]) {
 }
 
 // ---------------------------------------------------------------------------
-// Line smoother with twisted elimination, one column per thread.  The
-// tridiagonal system of a column (Algorithm Thomas, excess form) is eliminated
-// from both ends at once: levels 0..m-1 upwards and levels nz-1..m downwards
-// (m = nz/2) as the two halves of packed FP32x2 arithmetic.  Step s handles
+// Line smoother with twisted elimination.  The tridiagonal system of a column
+// (Algorithm Thomas, excess form) is eliminated from both ends at once: levels
+// 0..m-1 upwards and levels nz-1..m downwards (m = nz/2).  Step s handles
 // levels k = s and k' = nz-1-s.  The halves meet at the face between m-1 and
 // m, where the two remaining equations
 //     x_{m-1} = f'_{m-1} + c'_{m-1} x_m,   x_m = g'_m + d'_m x_{m-1}
@@ -419,14 +418,21 @@ __device__ __forceinline__ void tm_ld<8>(unsigned taddr, unsigned (&v)[16]) {
 // cancellation as rho_b + c' rho_t (rho = eps / m, the excess ratios of the
 // two last pivots); the back substitution then runs outwards.  Against
 // one-sided elimination this halves the sequential sweep, so the parked f'
-// and the iterate the back substitution re-reads stay in L2 for half as long,
-// and a warp holds 32 columns instead of 64: the L2 working set per unit of
-// throughput drops fourfold, which lets more warps run without spilling it to
-// DRAM.  Data movement per warp and step: the own rows of both levels with one
-// halo column each side, their b and rows j-1, j+1 (68 aligned 16-byte
-// cp.async chunks) into an FR-step shared-memory ring.  Pivots are recomputed
-// in the back substitution from one checkpoint per FR-step block (the same
-// instructions, so the same values).
+// and the iterate the back substitution re-reads stay in L2 for half as long.
+//
+// Work of a warp: 32 consecutive columns.  Lane p + 16 h (p < 16) eliminates
+// half h (0 bottom, 1 top) of the adjacent columns c0 + 2p and c0 + 2p + 1 as
+// the two lanes of packed FP32x2 arithmetic, so every value a step reads from
+// the staging ring (own pair, rows j-1 and j+1, b, the next level) is one
+// 64-bit shared load, and the back substitution stores pairs.  The two halves
+// of a column meet through one exchange between lanes p and p + 16.  A pair
+// never straddles a row or a panel edge (n is even), so only its outer halo
+// (west of the first column, east of the second) can lie off the staged row.
+// Data movement per warp and step: the own rows of both levels with one halo
+// column each side, their b and rows j-1, j+1 (68 aligned 16-byte cp.async
+// chunks) into an FR-step shared-memory ring; lane l copies for column c0 + l.
+// Pivots are recomputed in the back substitution from one checkpoint per
+// FR-step block (the same instructions, so the same values).
 // ---------------------------------------------------------------------------
 constexpr int kTT = 128;                      // threads per CTA (one column each)
 constexpr int kLvF = 136;                     // floats per warp and level: [own 40][b 32][j-1 32][j+1 32]
@@ -442,18 +448,23 @@ __host__ __device__ inline size_t tw_smem_bytes(int max_nz, int fr, bool aln) {
     return size_t(fr) * (kTT / 32) * kSlotF * 4 +          // ring
            (aln ? 0 : size_t(fr) * 4 * kTT * 4) +          // neighbours off the staged rows
            size_t(max_nz / 2 / fr) * kTT * 8 +             // pivot checkpoints
-           size_t(max_nz / 2) * 16 +                       // (V_k, V_k') and (g_{k+1}, g_k')
+           size_t(max_nz / 2) * 16 +                       // per half (V, g) of every step
            16;                                             // TMEM base address
 }
 
 // TM: the parked f' lives in tensor memory instead of the output buffer, one
-// column per elimination step and half (lane = thread).  Columns for a launch
-// whose items have at most max_nz levels (a power of two, 32 .. 512).
+// column per elimination step and column of the thread's pair (lane = thread).
+// Columns for a launch whose items have at most max_nz levels (a power of two,
+// 32 .. 512).
 constexpr int kTwTmemMaxNz = 256;
 __host__ __device__ inline int tw_tmem_cols(int max_nz) {
     int c = 32;
     while (c < max_nz) c *= 2;
     return c;
+}
+
+__device__ __forceinline__ float2 lds2(const float *p) {
+    return *reinterpret_cast<const float2 *>(p);
 }
 
 template <int ZERO, int FR, bool ALN, bool TM>
@@ -464,30 +475,34 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     float *ring = reinterpret_cast<float *>(smem_raw);
     float *fbr = ring + FR * (kTT / 32) * kSlotF;
     float2 *cpt = reinterpret_cast<float2 *>(fbr + (ALN ? 0 : FR * 4 * kTT));
-    float2 *VP = cpt + (max_nz / 2 / FR) * kTT;
-    float2 *GH = VP + max_nz / 2;
-    unsigned *tm_sh = reinterpret_cast<unsigned *>(GH + max_nz / 2);
+    float2 *VG = cpt + (max_nz / 2 / FR) * kTT;  // [half][step]: (V_k, g toward the next level)
+    unsigned *tm_sh = reinterpret_cast<unsigned *>(VG + max_nz);
     const Item it = items[blockIdx.x];
     const Lv<float> &d = L[it.lv];
     const int nc = d.ncol, nz = d.nz, n = d.n, m = nz / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c = it.col0 + tid;
     const int c0w = it.col0 + 32 * warp;
-    const bool active = c < nc;
+    const int c = c0w + lane;      // the column this lane stages
+    const int h = lane >> 4;       // the half this lane eliminates
+    const int p = lane & 15;
+    const int cA = c0w + 2 * p;    // its pair of columns: cA, cA + 1
+    const bool active = cA < nc;   // ncol % 4 == 0: both or neither
     // red-black half-sweep: a column of the other colour is carried over (its
     // lane still runs the elimination, in step with the warp, but stores the
-    // iterate it read instead)
-    const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
+    // iterate it read instead); the two columns of a pair differ in colour
+    const bool updA = it.colour == 0 || column_colour(cA, n) == it.colour - 1;
+    const bool updB = it.colour == 0 || column_colour(cA + 1, n) == it.colour - 1;
     constexpr bool zero = ZERO == 1;
     const unsigned tm_cols = TM ? unsigned(tw_tmem_cols(max_nz)) : 0u;
     if (TM && warp == 0) tm_alloc(tm_sh, tm_cols);
     for (int i = tid; i < m; i += kTT) {
-        VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
-        GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
+        VG[i] = make_float2(d.V[i], d.g[i + 1]);
+        VG[m + i] = make_float2(d.V[nz - 1 - i], d.g[nz - 1 - i]);
     }
     if (TM) tm_fence_before();
     __syncthreads();
     if (TM) tm_fence_after();
+    const float2 *VGh = VG + h * m;
     const unsigned tm0 = TM ? *tm_sh : 0u;
     const unsigned tm = tm0 + (unsigned(32 * warp) << 16);  // this warp's lanes
     const float *__restrict__ u = d.u[it.in];
@@ -496,24 +511,26 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     const size_t snc = size_t(nc);
     const size_t top0 = size_t(nz - 1) * snc;  // offset of level nz-1
 
-    float A = 1.f, sv = 1.f;
+    float2 A = f2(1.f), sv = f2(1.f);
     float2 t0 = f2(0.f), t1 = f2(0.f), t2 = f2(0.f), t3 = f2(0.f);
-    int4 nbr = make_int4(0, 0, 0, 0);
+    int4 nbA = make_int4(0, 0, 0, 0), nbB = nbA;
     if (active) {
-        const Column<float> k0 = load_column(d, c);
-        A = k0.A;
-        sv = k0.s;
-        t0 = f2(k0.t0);
-        t1 = f2(k0.t1);
-        t2 = f2(k0.t2);
-        t3 = f2(k0.t3);
-        nbr = k0.nb;
+        const Column<float> ka = load_column(d, cA), kb2 = load_column(d, cA + 1);
+        A = make_float2(ka.A, kb2.A);
+        sv = make_float2(ka.s, kb2.s);
+        t0 = make_float2(ka.t0, kb2.t0);
+        t1 = make_float2(ka.t1, kb2.t1);
+        t2 = make_float2(ka.t2, kb2.t2);
+        t3 = make_float2(ka.t3, kb2.t3);
+        nbA = ka.nb;
+        nbB = kb2.nb;
     }
     // Neighbours off the staged rows (panel edges, periodic wrap, rows that
-    // change inside the warp): at most one horizontal (hd 0 west, 1 east) and
-    // one vertical (vd 2 south, 3 north) per column when n >= 4.
+    // change inside the warp) of the staged column c: at most one horizontal
+    // (hd 0 west, 1 east) and one vertical (vd 2 south, 3 north) when n >= 4.
     int hd = -1, vd = -1, hc = 0, vc = 0;
-    if (active && !zero) {
+    if (c < nc && !zero) {
+        const int4 nbr = d.nbr[c];
         if (nbr.x != c - 1) { hd = 0; hc = nbr.x; }
         if (nbr.y != c + 1) { hd = 1; hc = nbr.y; }
         if (nbr.z != c - n) { vd = 2; vc = nbr.z; }
@@ -526,6 +543,12 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     const bool skip_e = ALN && __shfl_sync(0xffffffffu, hd == 1, 31);
     const bool skip_s = ALN && __shfl_sync(0xffffffffu, vd == 2, 0);
     const bool skip_n = ALN && __shfl_sync(0xffffffffu, vd == 3, 0);
+    // !ALN: which of the pair's neighbours come from the separate buffer
+    const bool ok = active && !zero;
+    const bool offW = ok && nbA.x != cA - 1;   // west of cA
+    const bool offE = ok && nbB.y != cA + 2;   // east of cA + 1
+    const bool offSA = ok && nbA.z != cA - n, offNA = ok && nbA.w != cA + n;
+    const bool offSB = ok && nbB.z != cA + 1 - n, offNB = ok && nbB.w != cA + 1 + n;
 
     // chunk q of a step's 68: 0..33 level k, 34..67 level k'; within a level
     // 0..9 own row with halo, 10..17 b, 18..25 row j-1, 26..33 row j+1
@@ -607,18 +630,22 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
 
 #pragma unroll
     for (int j = 0; j < FR - 1; ++j) issue(j);
-    const int own = kOwnT + 4 + lane;  // this thread's column in an own row
+    const int own = kOwnT + 4 + 2 * p;            // the pair's first column in an own row
+    const int hv = h * kLvF;                      // this half's level within a ring slot
+    // !ALN: the pair's neighbours in the separate buffer, [slot][h B, v B, h T, v T][column]
+    const float *fbp = fbr + warp * 32 + 2 * p + (h ? 2 : 0) * kTT;
     constexpr int kStride = (kTT / 32) * kSlotF;  // floats between ring slots
     float2 u0 = f2(0.f), um = f2(0.f);
     if (!zero) {
         cp_async_wait<FR - 2>();
         __syncwarp();
-        u0 = make_float2(wring[own], wring[kLvF + own]);
+        u0 = lds2(wring + hv + own);
     }
     float2 ratio = f2(0.f), fp = f2(0.f), lo = f2(0.f), lo_g = f2(0.f);
     Piv2 pv;
     pv.cp = pv.inv = pv.ratio_next = f2(0.f);
-    float *fpb = un + c, *fpt = un + top0 + c;
+    float *fpp = un + (h ? top0 : 0) + cA;
+    const long long fadv = h ? -(long long)nc : (long long)nc;
     const int nblk = m / FR;
 #pragma unroll 1
     for (int kb = 0; kb < nblk; ++kb) {
@@ -636,30 +663,31 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
                 cp_async_wait_upto(FR - 2 - j);
             }
             __syncwarp();
-            const float *sk = wring + j * kStride;
-            float2 r = make_float2(sk[kBT + lane], sk[kLvF + kBT + lane]);
-            const float2 hi_g = GH[s], Vp = VP[s];
-            const float2 ucur = u0;  // the iterate at levels k, k' (carried over when !upd)
+            const float *sk = wring + j * kStride + hv;  // this half's level k or k'
+            float2 r = lds2(sk + kBT + 2 * p);
+            const float2 vg = VGh[s];
+            const float2 Vp = f2(vg.x), hi_g = f2(vg.y);
+            const float2 ucur = u0;  // the iterate at this level (carried over when !upd)
             if (!zero) {
                 float2 up;
                 if (last && j == FR - 1) {
                     // the meeting step: the next level of each half is the other half's
-                    up = make_float2(sk[kLvF + own], sk[own]);
+                    up = lds2(wring + j * kStride + (kLvF - hv) + own);
                 } else {
-                    const float *sn = wring + ((j + 1) % FR) * kStride;
-                    up = make_float2(sn[own], sn[kLvF + own]);
+                    up = lds2(wring + ((j + 1) % FR) * kStride + hv + own);
                 }
-                float2 nw = make_float2(sk[own - 1], sk[kLvF + own - 1]);
-                float2 ne = make_float2(sk[own + 1], sk[kLvF + own + 1]);
-                float2 ns = make_float2(sk[kJmT + lane], sk[kLvF + kJmT + lane]);
-                float2 nn = make_float2(sk[kJpT + lane], sk[kLvF + kJpT + lane]);
+                float2 nw = make_float2(sk[own - 1], u0.x);
+                float2 ne = make_float2(u0.y, sk[own + 2]);
+                float2 ns = lds2(sk + kJmT + 2 * p);
+                float2 nn = lds2(sk + kJpT + 2 * p);
                 if (!ALN && warp_fb) {
-                    const float2 vh = make_float2(fbt[(j * 4 + 0) * kTT], fbt[(j * 4 + 2) * kTT]);
-                    const float2 vv = make_float2(fbt[(j * 4 + 1) * kTT], fbt[(j * 4 + 3) * kTT]);
-                    nw = hd == 0 ? vh : nw;
-                    ne = hd == 1 ? vh : ne;
-                    ns = vd == 2 ? vv : ns;
-                    nn = vd == 3 ? vv : nn;
+                    const float *fj = fbp + j * 4 * kTT;
+                    if (offW) nw.x = fj[0];
+                    if (offE) ne.y = fj[1];
+                    if (offSA) ns.x = fj[kTT];
+                    if (offNA) nn.x = fj[kTT];
+                    if (offSB) ns.y = fj[kTT + 1];
+                    if (offNB) nn.y = fj[kTT + 1];
                 }
                 float2 horiz = __fmul2_rn(t0, sub2(u0, nw));
                 horiz = __ffma2_rn(t1, sub2(u0, ne), horiz);
@@ -667,37 +695,51 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
                 horiz = __ffma2_rn(t3, sub2(u0, nn), horiz);
                 float2 vert = __fmul2_rn(hi_g, sub2(u0, up));
                 vert = __ffma2_rn(lo_g, sub2(u0, um), vert);
-                float2 Au = __fmul2_rn(f2(A), __fmul2_rn(Vp, u0));
+                float2 Au = __fmul2_rn(A, __fmul2_rn(Vp, u0));
                 Au = __ffma2_rn(Vp, horiz, Au);
-                Au = __ffma2_rn(f2(A), vert, Au);
+                Au = __ffma2_rn(A, vert, Au);
                 r = sub2(r, Au);
                 um = u0;
                 u0 = up;
             }
-            const float2 hi = __fmul2_rn(f2(A), hi_g);
-            pv = pivot2(__fmul2_rn(Vp, f2(sv)), lo, hi, ratio);
+            const float2 hi = __fmul2_rn(A, hi_g);
+            pv = pivot2(__fmul2_rn(Vp, sv), lo, hi, ratio);
             fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
             if (TM) {
                 tm_st2(tm + 2u * unsigned(s), fp);
             } else {
-                if (active) {
-                    *fpb = upd ? fp.x : ucur.x;
-                    *fpt = upd ? fp.y : ucur.y;
-                }
-                fpb += snc;
-                fpt -= snc;
+                if (active)
+                    *reinterpret_cast<float2 *>(fpp) =
+                        make_float2(updA ? fp.x : ucur.x, updB ? fp.y : ucur.y);
+                fpp += fadv;
             }
             ratio = pv.ratio_next;
             lo = hi;
             lo_g = hi_g;
         }
     }
-    // meeting of the halves: x_{m-1} and x_m from the two last equations
+    // meeting of the halves: x_{m-1} and x_m from the two last equations, per
+    // column, from this lane's and the partner lane's last pivots
     float2 x;
     {
-        const float den = __fmaf_rn(pv.cp.x, pv.ratio_next.y, pv.ratio_next.x);
-        const float xb = __fmul_rn(__fmaf_rn(pv.cp.x, fp.y, fp.x), rcp(den));
-        x = make_float2(xb, __fmaf_rn(pv.cp.y, xb, fp.y));
+        const float2 ofp = make_float2(__shfl_xor_sync(0xffffffffu, fp.x, 16),
+                                       __shfl_xor_sync(0xffffffffu, fp.y, 16));
+        const float2 ocp = make_float2(__shfl_xor_sync(0xffffffffu, pv.cp.x, 16),
+                                       __shfl_xor_sync(0xffffffffu, pv.cp.y, 16));
+        const float2 ort = make_float2(__shfl_xor_sync(0xffffffffu, pv.ratio_next.x, 16),
+                                       __shfl_xor_sync(0xffffffffu, pv.ratio_next.y, 16));
+        const float2 fb_ = h ? ofp : fp, cb_ = h ? ocp : pv.cp, rb_ = h ? ort : pv.ratio_next;
+        const float2 ft_ = h ? fp : ofp, ct_ = h ? pv.cp : ocp, rt_ = h ? pv.ratio_next : ort;
+        const float fbv[2] = {fb_.x, fb_.y}, cbv[2] = {cb_.x, cb_.y}, rbv[2] = {rb_.x, rb_.y};
+        const float ftv[2] = {ft_.x, ft_.y}, ctv[2] = {ct_.x, ct_.y}, rtv[2] = {rt_.x, rt_.y};
+        float xb[2], xt[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float den = __fmaf_rn(cbv[q], rtv[q], rbv[q]);
+            xb[q] = __fmul_rn(__fmaf_rn(cbv[q], ftv[q], fbv[q]), rcp(den));
+            xt[q] = __fmaf_rn(ctv[q], xb[q], ftv[q]);
+        }
+        x = h ? make_float2(xt[0], xt[1]) : make_float2(xb[0], xb[1]);
     }
     __threadfence_block();  // the f' stores of this warp are seen by its copies below
     __syncwarp();
@@ -721,24 +763,26 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     };
 #pragma unroll
     for (int j = 0; j < FR - 1; ++j) issue_back(j);
-    float *uob = un + size_t(m - 1) * snc + c, *uot = un + size_t(m) * snc + c;
+    float *uo_p = un + size_t(h ? m : m - 1) * snc + cA;
+    const long long uadv = h ? (long long)nc : -(long long)nc;
 #pragma unroll 1
     for (int kb = nblk - 1; kb >= 0; --kb) {
         float2 cpr[FR];
         {
             float2 rt = active ? cpt[kb * kTT + tid] : f2(0.f);
-            float2 l0 = kb == 0 ? f2(0.f) : __fmul2_rn(f2(A), GH[kb * FR - 1]);
+            float2 l0 = kb == 0 ? f2(0.f) : __fmul2_rn(A, f2(VGh[kb * FR - 1].y));
 #pragma unroll
             for (int j = 0; j < FR; ++j) {
                 const int s = kb * FR + j;
-                const float2 h1 = __fmul2_rn(f2(A), GH[s]);
-                const Piv2 q = pivot2(__fmul2_rn(VP[s], f2(sv)), l0, h1, rt);
+                const float2 vg = VGh[s];
+                const float2 h1 = __fmul2_rn(A, f2(vg.y));
+                const Piv2 q = pivot2(__fmul2_rn(f2(vg.x), sv), l0, h1, rt);
                 cpr[j] = q.cp;
                 rt = q.ratio_next;
                 l0 = h1;
             }
         }
-        unsigned fv[2 * FR];  // TM: f' and g' of the block's steps
+        unsigned fv[2 * FR];  // TM: f' of the block's steps, both columns of the pair
         if constexpr (TM) tm_ld<FR>(tm + 2u * unsigned(kb * FR), fv);
         const bool last = kb == 0;
 #pragma unroll
@@ -759,22 +803,15 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             if constexpr (TM)
                 fk = make_float2(__uint_as_float(fv[2 * jj]), __uint_as_float(fv[2 * jj + 1]));
             else
-                fk = make_float2(sk[lane], sk[32 + lane]);
-            const float2 uo = zero ? f2(0.f) : make_float2(sk[64 + lane], sk[96 + lane]);
+                fk = lds2(sk + 32 * h + 2 * p);
+            const float2 uo = zero ? f2(0.f) : lds2(sk + 64 + 32 * h + 2 * p);
             if (s != m - 1) x = __ffma2_rn(cpr[jj], x, fk);
             const float2 un2 = __ffma2_rn(f2(rho), x, uo);
-            if (TM) {
-                // every column is written here, the iterate carried over where !upd
-                if (active) {
-                    __stcs(uob, upd ? un2.x : uo.x);
-                    __stcs(uot, upd ? un2.y : uo.y);
-                }
-            } else if (active && upd) {
-                __stcs(uob, un2.x);
-                __stcs(uot, un2.y);
-            }
-            uob -= snc;
-            uot += snc;
+            // every column is written, the iterate carried over where !upd
+            if (active)
+                __stcs(reinterpret_cast<float2 *>(uo_p),
+                       make_float2(updA ? un2.x : uo.x, updB ? un2.y : uo.y));
+            uo_p += uadv;
         }
     }
     cp_async_wait<0>();
