@@ -113,11 +113,15 @@ class ClockSampler:
 
 
 _oracle_barrier = None
+# every CPU this process may use, taken before the process is bound to the CPUs
+# local to its GPU: the oracle's CPU baseline runs on all of them
+HOST_CPUS_ALL = sorted(os.sched_getaffinity(0))
 
 
-def _oracle_init(barrier):
+def _oracle_init(barrier, cpus):
     global _oracle_barrier
     _oracle_barrier = barrier
+    os.sched_setaffinity(0, cpus)
 
 
 def _oracle_one(job):
@@ -148,15 +152,16 @@ def oracle_rate_parallel(sample, vcycles, procs=None):
     seconds, processes, description)."""
     import multiprocessing as mp
     if procs is None:
-        procs = max(1, len(os.sched_getaffinity(0)))
+        procs = max(1, len(HOST_CPUS_ALL))
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(procs)
-    with ctx.Pool(procs, initializer=_oracle_init, initargs=(barrier,)) as pool:
+    with ctx.Pool(procs, initializer=_oracle_init, initargs=(barrier, HOST_CPUS_ALL)) as pool:
         res = pool.map(_oracle_one, [(sample, vcycles, m) for m in range(procs)])
     work = sum(r[0] for r in res)
     dt = max(r[1] for r in res)
     kind, n, nz = sample[0], sample[1], sample[2]
-    desc = (f"oracle (plain C, FP64, one thread per process) on {procs} processes at once, "
+    desc = (f"oracle (plain C, FP64, one thread per process) on {procs} processes at once "
+            f"(host CPUs {HOST_CPUS_ALL[0]}-{HOST_CPUS_ALL[-1]}), "
             f"each {vcycles} V-cycle(s) + residual on the {'sphere 6x' if kind == 1 else 'box '}"
             f"{n}x{n}x{nz} graded grid ({work // (procs * vcycles)} unknowns, its own "
             f"right-hand side)")
@@ -406,6 +411,7 @@ def run_ours(args, rank, world, local_rank):
             "autotuned_smoother_ctas_per_sm": tuned_ctas,
             "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
             "final_rel_residual": final_rel, "time_to_rtol_ms": ms / args.steps,
+            "rel_error_est": res.rel_error_est,
             "l2_policy": "inputs larger than L2 (FP32 hierarchy %.1f GB)" % (N * 16 / 3 * 4 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -455,6 +461,8 @@ def run_accuracy(torch, stream, workload):
         stream.synchronize()
         out[name] = {"ms": e0.elapsed_time(e1), "vcycles": res.iterations,
                      "rel_residual": res.rel_residual, "status": int(st)}
+        if name == "mixed":
+            out[name]["rel_error_est"] = res.rel_error_est
         sv.close()
     with torch.cuda.stream(stream):
         err = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
@@ -589,7 +597,8 @@ def run_ensemble(torch, stream, members=32, n=128, nz=64, rtol=1e-8, reps=3):
     per-member omega^2 (log-uniform [1e-3, 1e-1]) and lambda (uniform [0.5, 5]),
     uniform right-hand sides; one batched mixed-precision solve (one launch per
     kernel and level over all members) against the same solves done one after
-    another in plain FP64 multigrid."""
+    another in plain FP64 multigrid, and the same mixed-precision solves one
+    after another (which separates the gain of batching from that of precision)."""
     from paper_1307_2036_gb300 import ellsolve, inputs
     w2s, lams = inputs.member_params(members)
     r = inputs.radial_levels(nz, graded=True)
@@ -611,6 +620,18 @@ def run_ensemble(torch, stream, members=32, n=128, nz=64, rtol=1e-8, reps=3):
     batched_s = e0.elapsed_time(e1) / 1e3 / reps
     worst = max(x.rel_residual for x in res)
     cycles = [x.iterations for x in res]
+    # the same mixed-precision solves one member after another: the gain of
+    # batching alone
+    for m in range(members):
+        sv[m].solve(fs[m], xs[m], rtol=rtol, maxit=60)  # warm-up (each handle's own plan)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for m in range(members):
+            sv[m].solve(fs[m], xs[m], rtol=rtol, maxit=60)
+    e1.record(stream)
+    stream.synchronize()
+    seq_mixed_s = e0.elapsed_time(e1) / 1e3 / reps
     # plain FP64, one member after another
     with torch.cuda.stream(stream):
         p64 = [ellsolve.Solver(1, n, nz, r, float(w2s[m]), float(lams[m]) ** 2, precision=0,
@@ -628,85 +649,145 @@ def run_ensemble(torch, stream, members=32, n=128, nz=64, rtol=1e-8, reps=3):
     seq_s = e0.elapsed_time(e1) / 1e3
     return {"workload": f"{members} members, cubed sphere 6x{n}x{n}x{nz}, rtol {rtol}",
             "batched_mixed_solves_per_s": members / batched_s,
+            "sequential_mixed_solves_per_s": members / seq_mixed_s,
             "sequential_fp64_solves_per_s": members / seq_s,
             "speedup": seq_s / batched_s,
+            "batching_gain": seq_mixed_s / batched_s,
+            "precision_gain": seq_s / seq_mixed_s,
             "batched_vcycles_per_member": [min(cycles), max(cycles)],
             "fp64_vcycles_per_member": [min(it64), max(it64)],
             "worst_rel_residual": worst}
 
 
-def run_serving(torch, stream, count, rate=200.0, budget=96 << 30, slots=16):
-    """Config 5 (bounded sample of `count` requests): Poisson arrivals at `rate`
-    per second, n in {48, 96, 192, 384}, nz in {32, 64, 128}, tol in {1e-5,
-    1e-10}, omega^2 and lambda as in config 4.  Requests go through the
-    continuous-batching server; latency is submit -> completion as the library
-    measures it.  Baseline: plain FP64 multigrid one request at a time in FIFO
-    order, service times measured on the first requests and queued against the
-    same arrivals."""
+def _serve(torch, stream, ellsolve, inputs, req, shapes, budget, slots):
+    """Submit the requests of `req` at their arrival times to a fresh server;
+    between submissions poll the outstanding ones without waiting, so that a
+    finished request's solution buffer is released at once (the device holds
+    the solution of every outstanding request).  Returns per-request latency
+    (submit -> completion, as the library measures it), status and wall time."""
+    import numpy as np
+    count = len(req["arrival"])
+    srv = ellsolve.Server(budget, slots, stream=stream.cuda_stream)
+    lat = np.zeros(count)
+    status = np.zeros(count, dtype=np.int64)
+    outstanding = {}  # ticket -> (index, x)
+
+    def drain(wait):
+        for t in list(outstanding):
+            st, res = srv.poll(t, timeout_us=-1 if wait else 0)
+            if st == ellsolve.PENDING:
+                continue
+            i, _ = outstanding.pop(t)
+            lat[i], status[i] = res.seconds, st
+    t0 = time.perf_counter()
+    for i in range(count):
+        due = t0 + float(req["arrival"][i])
+        while True:
+            drain(False)
+            now = time.perf_counter()
+            if now >= due:
+                break
+            time.sleep(min(due - now, 2e-3))
+        n, nz = int(req["n"][i]), int(req["nz"][i])
+        with torch.cuda.stream(stream):
+            x = torch.zeros_like(shapes[(n, nz)])
+        stream.synchronize()
+        t = srv.submit(1, n, nz, inputs.radial_levels(nz, graded=True), float(req["omega2"][i]),
+                       float(req["lam"][i]) ** 2, shapes[(n, nz)], x, rtol=float(req["tol"][i]),
+                       maxit=80)
+        outstanding[t] = (i, x)
+    drain(True)
+    wall = time.perf_counter() - t0
+    srv.close()
+    return lat, status, wall
+
+
+def _fifo(arrival, service):
+    """One-at-a-time FIFO queue over the arrivals: latency of every request."""
+    import numpy as np
+    done, lat = 0.0, np.zeros(len(arrival))
+    for i, (a, s) in enumerate(zip(arrival, service)):
+        done = max(float(a), done) + float(s)
+        lat[i] = done - float(a)
+    return lat, done - float(arrival[0])
+
+
+def run_serving(torch, stream, count, rate=200.0, low_count=1000, low_rate=60.0,
+                budget=64 << 30, slots=16):
+    """Config 5 through the continuous-batching server: Poisson arrivals, n in
+    {48, 96, 192, 384}, nz in {32, 64, 128}, tol in {1e-5, 1e-10}, omega^2 and
+    lambda as in config 4.  Two runs: `count` requests offered at `rate` per
+    second (config 5's rate, above the server's capacity, so the queue grows;
+    `count` is bounded by the device memory the outstanding requests'
+    solution buffers need), and `low_count` requests at `low_rate`, below
+    capacity.  Baseline: plain FP64 multigrid one request at a time in FIFO
+    order over the same arrivals, with the service time of each (n, nz, tol)
+    class measured once on the GPU (the class's first request)."""
     import numpy as np
 
     from paper_1307_2036_gb300 import ellsolve, inputs
-    req = inputs.request_stream(count, rate=rate)
-    shapes = {}
-    with torch.cuda.stream(stream):
-        for i in range(count):
-            key = (int(req["n"][i]), int(req["nz"][i]))
-            if key not in shapes:
-                shapes[key] = torch.tensor(
-                    inputs.uniform_pm1((key[1], 6, key[0], key[0]), member=1000 + len(shapes)),
-                    device="cuda")
-        xs = [torch.zeros_like(shapes[(int(req["n"][i]), int(req["nz"][i]))]) for i in range(count)]
-    stream.synchronize()
-    srv = ellsolve.Server(budget, slots, stream=stream.cuda_stream)
-    t0 = time.perf_counter()
-    tickets = []
-    for i in range(count):
-        due = t0 + float(req["arrival"][i])
-        now = time.perf_counter()
-        if due > now:
-            time.sleep(due - now)
-        n, nz = int(req["n"][i]), int(req["nz"][i])
-        tickets.append(srv.submit(1, n, nz, inputs.radial_levels(nz, graded=True),
-                                  float(req["omega2"][i]), float(req["lam"][i]) ** 2,
-                                  shapes[(n, nz)], xs[i], rtol=float(req["tol"][i]), maxit=80))
-    lat, counts = [], {"ok": 0, "not_converged": 0, "error": 0}
-    for t in tickets:
-        st, res = srv.poll(t, timeout_us=-1)
-        lat.append(res.seconds)
-        counts["ok" if st == ellsolve.OK else
-               "not_converged" if st == ellsolve.NOT_CONVERGED else "error"] += 1
-    wall = time.perf_counter() - t0
-    srv.close()
-    lat = np.array(lat)
-    # FIFO plain-FP64 baseline on the first requests
-    nb = min(count, 24)
-    svc = []
-    for i in range(nb):
-        n, nz = int(req["n"][i]), int(req["nz"][i])
+    runs = {}
+    fifo_cache = {}
+    for name, cnt, rt, seed_off in (("offered_at_config_rate", count, rate, 0),
+                                    ("below_capacity", low_count, low_rate, 1)):
+        req = inputs.request_stream(cnt, rate=rt, seed=inputs.DEFAULT_SEED + seed_off)
+        shapes = {}
         with torch.cuda.stream(stream):
-            p = ellsolve.Solver(1, n, nz, inputs.radial_levels(nz, graded=True),
-                                float(req["omega2"][i]), float(req["lam"][i]) ** 2, precision=0,
-                                stream=stream.cuda_stream)
+            for i in range(cnt):
+                key = (int(req["n"][i]), int(req["nz"][i]))
+                if key not in shapes:
+                    shapes[key] = torch.tensor(
+                        inputs.uniform_pm1((key[1], 6, key[0], key[0]), member=1000 + len(shapes)),
+                        device="cuda")
         stream.synchronize()
-        a = time.perf_counter()
-        p.solve(shapes[(n, nz)], xs[i], rtol=float(req["tol"][i]), maxit=100)
-        stream.synchronize()
-        svc.append(time.perf_counter() - a)
-        del p
-    done, base = 0.0, []
-    for i in range(nb):
-        start = max(float(req["arrival"][i]), done)
-        done = start + svc[i]
-        base.append(done - float(req["arrival"][i]))
-    base = np.array(base)
-    return {"workload": f"{count} requests, Poisson {rate:g}/s, n in 48..384, nz in 32..128, "
-                        f"tol 1e-5/1e-10; server {slots} slots, {budget >> 30} GiB",
-            "solves_per_s": count / wall, "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "status_counts": counts,
-            "note": "not_converged: 1e-10 requests whose FP64 attainable residual is above 1e-10",
-            "fp64_fifo_baseline": {"requests": nb, "solves_per_s": nb / float(np.sum(svc)),
+        lat, status, wall = _serve(torch, stream, ellsolve, inputs, req, shapes, budget, slots)
+        # FP64 FIFO baseline: service time per (n, nz, tol) class
+        service = np.zeros(cnt)
+        for i in range(cnt):
+            key = (int(req["n"][i]), int(req["nz"][i]), float(req["tol"][i]))
+            if key not in fifo_cache:
+                n, nz, tol = key
+                with torch.cuda.stream(stream):
+                    p = ellsolve.Solver(1, n, nz, inputs.radial_levels(nz, graded=True),
+                                        float(req["omega2"][i]), float(req["lam"][i]) ** 2,
+                                        precision=0, stream=stream.cuda_stream)
+                    xb = torch.zeros_like(shapes[(n, nz)])
+                stream.synchronize()
+                a = time.perf_counter()
+                p.solve(shapes[(n, nz)], xb, rtol=tol, maxit=100)
+                stream.synchronize()
+                fifo_cache[key] = time.perf_counter() - a
+                del p, xb
+            service[i] = fifo_cache[key]
+        base, base_span = _fifo(req["arrival"], service)
+        ok = status == ellsolve.OK
+        nc = status == ellsolve.NOT_CONVERGED
+        runs[name] = {
+            "requests": cnt, "offered_per_s": rt,
+            "achieved_solves_per_s": cnt / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "status_counts": {"ok": int(ok.sum()), "not_converged": int(nc.sum()),
+                              "error": int((~ok & ~nc).sum())},
+            "not_converged_requests": [
+                {"n": int(req["n"][i]), "nz": int(req["nz"][i]), "tol": float(req["tol"][i]),
+                 "omega2": float(req["omega2"][i]), "lambda": float(req["lam"][i])}
+                for i in np.nonzero(nc)[0][:8]],
+            "fp64_fifo_baseline": {"solves_per_s": cnt / base_span,
                                    "p50_latency_s": float(np.percentile(base, 50)),
                                    "p99_latency_s": float(np.percentile(base, 99))}}
+        del shapes
+        torch.cuda.empty_cache()
+    return {"workload": "config 5 requests: n in 48..384, nz in 32..128, tol 1e-5/1e-10; "
+                        f"server {slots} slots, {budget >> 30} GiB budget",
+            "sample": (f"{count} of config 5's 10,000 requests at {rate:g}/s (the queue grows "
+                       "above capacity and every outstanding request holds its solution "
+                       "buffer on the device, which bounds the sample), and "
+                       f"{low_count} requests at {low_rate:g}/s below capacity"),
+            "fp64_fifo_service": "plain FP64 multigrid, one solve per (n, nz, tol) class timed "
+                                 "on the GPU, queued FIFO against the same arrivals",
+            "note": "not_converged: 1e-10 requests whose FP64 attainable residual is above 1e-10",
+            **runs}
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
@@ -723,8 +804,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ensemble and serving measurements")
-    ap.add_argument("--serve-requests", type=int, default=200,
-                    help="requests in the bounded serving sample")
+    ap.add_argument("--serve-requests", type=int, default=1500,
+                    help="requests of the serving run at config 5's rate (bounded by the device "
+                         "memory that outstanding solution buffers need)")
     ap.add_argument("--inner-cycles", type=int, default=3,
                     help="FP32 V-cycles per FP64 refinement step")
     args = ap.parse_args()

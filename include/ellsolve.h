@@ -110,6 +110,17 @@ typedef struct {
     int iterations;      /* V-cycles (MG) or CG iterations done */
     double rel_residual; /* final ||b - A u|| / ||b|| (FP64) */
     double seconds;      /* wall time of the solve on the stream */
+    /* Estimate of the relative error ||x* - x|| / ||x*|| against the exact
+     * solution x* of the discrete problem, which the FP64 solvers approach.
+     * Mixed precision (precision 1): from the refinement updates of x, as
+     * q / (1 - q) ||dx_last|| / ||dx_first|| (the error left by a linearly
+     * contracting iteration; x starts at 0, so the first update is x* to
+     * within the first step's contraction), with q the last step's residual
+     * reduction scaled by how much more the error than the residual
+     * contracted in the step before (||dx_last|| / ||dx_prev|| against that
+     * step's residual reduction).  -1 for the FP64 multigrid and PCG solvers,
+     * which report the exact residual only. */
+    double rel_error_est;
 } ellsolve_result;
 
 /* Fill *o with the defaults listed above. */

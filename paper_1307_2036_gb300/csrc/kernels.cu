@@ -1455,7 +1455,8 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                                                    const double *__restrict__ scale,
                                                    const int *__restrict__ sel, int nmembers,
                                                    int max_nz, double *__restrict__ partials,
-                                                   double *__restrict__ partials2) {
+                                                   double *__restrict__ partials2,
+                                                   double *__restrict__ partials3) {
     extern __shared__ float2 vg_sh[];  // (V_k hi, lo) [max_nz], (g_k hi, lo) [max_nz + 1]
     float2 *Vh = vg_sh, *gh = vg_sh + max_nz;
     const Item it = items[blockIdx.x];
@@ -1472,7 +1473,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
     }
     __syncthreads();
     const int c = it.col0 + threadIdx.x;
-    double acc = 0.0, acc2 = 0.0;
+    double acc = 0.0, acc2 = 0.0, acc3 = 0.0;
     const double sc = scale[it.lv], sn = scale[nmembers + it.lv];
     if (c < nc) {
         double *__restrict__ x = d.u[0];
@@ -1487,7 +1488,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
         const ff A = split_ff(col.A), S = split_ff(col.s);
         const ff T0 = split_ff(col.t0), T1 = split_ff(col.t1), T2 = split_ff(col.t2),
                  T3 = split_ff(col.t3);
-        float colsum = 0.f, magsum = 0.f;
+        float colsum = 0.f, magsum = 0.f, esum = 0.f;
         float e0 = __ldg(e + c);
         ff flux_lo = {0.f, 0.f};
         // the loads of kTB levels are issued before their arithmetic
@@ -1548,20 +1549,25 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                     A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
                 magsum = __fmaf_rn(mag, mag, magsum);
                 __stcs(x + o + c, xv[j] + f32_to_f64_pow2(e0, kx));
+                esum = __fmaf_rn(e0, e0, esum);
                 flux_lo = flux_hi;
                 e0 = ep;
             }
         }
         acc = double(colsum);
         acc2 = double(magsum);
+        acc3 = double(esum);
     }
     const double inv2 = 1.0 / (sc * sc);
     const double t1 = block_sum(acc);
     __syncthreads();  // block_sum's shared slots are reused
     const double t2 = block_sum(acc2);
+    __syncthreads();
+    const double t3 = block_sum(acc3);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = t1 * inv2;
         partials2[blockIdx.x] = t2 * inv2;
+        partials3[blockIdx.x] = t3 * inv2;  // squared norm of the update of x
     }
 }
 
@@ -1569,13 +1575,15 @@ __global__ void __launch_bounds__(kBlk) k_ir_update(const Lv<double> *__restrict
                                                     const Lv<float> *__restrict__ L32,
                                                     const Item *__restrict__ items,
                                                     const double *__restrict__ scale,
-                                                    const int *__restrict__ sel, int want) {
+                                                    const int *__restrict__ sel, int want,
+                                                    double *__restrict__ partials3) {
     const Item it = items[blockIdx.x];
     if (sel[it.lv] != want) return;
     const Lv<double> &d = L64[it.lv];
     const int c = it.col0 + threadIdx.x;
     const int nc = d.ncol;
-    if (c >= nc) return;
+    double esum = 0.0;  // squared norm of the update e / scale
+    if (c < nc) {
     double *__restrict__ x = d.u[0];
     const float *__restrict__ e = L32[it.lv].u[it.in];
     // x += e / scale with scale = 2^-k: the conversion and the scaling are one
@@ -1594,17 +1602,29 @@ __global__ void __launch_bounds__(kBlk) k_ir_update(const Lv<double> *__restrict
                 ev[j] = __ldg(e + o);
                 xv[j] = x[o];
             }
+            float es = 0.f;
 #pragma unroll
             for (int j = 0; j < B; ++j)
-                if (l0 + j < d.nz) x[size_t(l0 + j) * nc + c] = xv[j] + f32_to_f64_pow2(ev[j], k);
+                if (l0 + j < d.nz) {
+                    x[size_t(l0 + j) * nc + c] = xv[j] + f32_to_f64_pow2(ev[j], k);
+                    es = __fmaf_rn(ev[j], ev[j], es);
+                }
+            esum += double(es);
         }
+        const double sc = scale[it.lv];
+        esum /= sc * sc;
     } else {
         const double inv = 1.0 / scale[it.lv];
         for (int l = 0; l < d.nz; ++l) {
             const size_t o = size_t(l) * nc + c;
-            x[o] += double(__ldg(e + o)) * inv;
+            const double dx = double(__ldg(e + o)) * inv;
+            x[o] += dx;
+            esum += dx * dx;
         }
     }
+    }
+    const double t = block_sum(esum);
+    if (threadIdx.x == 0) partials3[blockIdx.x] = t;
 }
 
 template <typename T>
@@ -2035,21 +2055,22 @@ cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<f
 
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,
-                             const int *sel, int want) {
+                             const int *sel, int want, double *partials3) {
     if (nitems <= 0) return cudaSuccess;
-    k_ir_update<<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want);
+    k_ir_update<<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials3);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ir_track(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                             const Item *items, int nitems, const double *scale, const int *sel,
-                            int nmembers, int max_nz, double *partials, double *partials2) {
+                            int nmembers, int max_nz, double *partials, double *partials2,
+                            double *partials3) {
     if (nitems <= 0) return cudaSuccess;
     const size_t bytes = size_t(2 * max_nz + 1) * sizeof(float2);
     cudaError_t e = set_smem(k_ir_track, bytes);
     if (e != cudaSuccess) return e;
     k_ir_track<<<nitems, kBlk, bytes, s>>>(L64, L32, items, scale, sel, nmembers, max_nz,
-                                           partials, partials2);
+                                           partials, partials2, partials3);
     return cudaGetLastError();
 }
 

@@ -73,18 +73,20 @@ cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<f
                                const Item *items, int nitems, const double *scale,
                                double *partials, int x_is_zero, const int *sel, int want,
                                double *partials2, int max_nz);
-// x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with sel[m] == want
+// x (L64[m].u[0]) += L32[m].u[item.in] / scale[m] for members with sel[m] == want;
+// partials3[item] = squared norm of the update
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,
-                             const int *sel, int want);
+                             const int *sel, int want, double *partials3);
 // Tracked refinement step for members with sel[m] == 1 (scale[m] = s,
 // scale[nmembers + m] = s_next, e = L32[m].u[item.in], rt = L64[m].aux):
 //   x += e / s;  rt = (rt - A e) s_next / s (double-float);  L32[m].b = hi(rt);
 //   partials[item] = sum of (rt - A e)^2 / s^2, partials2[item] = sum of the
-//   squared magnitudes (|A| |e|)^2 / s^2.
+//   squared magnitudes (|A| |e|)^2 / s^2, partials3[item] = sum of (e / s)^2.
 cudaError_t launch_ir_track(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                             const Item *items, int nitems, const double *scale, const int *sel,
-                            int nmembers, int max_nz, double *partials, double *partials2);
+                            int nmembers, int max_nz, double *partials, double *partials2,
+                            double *partials3);
 
 // b = A_P V_k f on every item (FP64 or FP32 output), partial sums of b^2.
 template <typename T>

@@ -387,6 +387,7 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
     upload(dfirst, first_dev, s);
     partials.alloc(size_t(std::max(outer_n, 1)) * sizeof(double));
     partials2.alloc(size_t(std::max(outer_n, 1)) * sizeof(double));
+    partials3.alloc(size_t(std::max(outer_n, 1)) * sizeof(double));
     norms.alloc(size_t(M) * 4 * sizeof(double));
     scales.alloc(size_t(2) * M * sizeof(double));
     std::vector<double> cnt(M), ones(M, 1.0);
@@ -399,7 +400,7 @@ void Plan::build(const std::vector<Problem *> &members, int prec) {
                                cudaMemcpyHostToDevice, s),
                "scales");
     check_cuda(cudaStreamSynchronize(s), "plan sync");
-    host_norms.assign(2 * M, 0.0);
+    host_norms.assign(3 * M, 0.0);
     if (hnorms_n < size_t(4 * M)) {
         if (hnorms) cudaFreeHost(hnorms);
         hnorms = nullptr;
@@ -808,11 +809,12 @@ static bool stagnated(const std::vector<double> &hist) {
 }
 
 static ellsolve_status finish(double rel, int it, double rtol, bool stag, ellsolve_result *res,
-                              double secs) {
+                              double secs, double err_est = -1.0) {
     if (res) {
         res->iterations = it;
         res->rel_residual = rel;
         res->seconds = secs;
+        res->rel_error_est = err_est;
     }
     if (!std::isfinite(rel)) {
         set_last_error("residual norm is not finite");
@@ -987,6 +989,7 @@ void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep
         r.active = true;
         r.iters = 0;
         r.hist.assign(1, 1.0);
+        r.dx_first = r.dx_prev = r.dx_last = 0.0;
     }
     ir_push_state(pl, run);
     ir_residual_norm(pl, m0, m1, keep_x ? 0 : 2);  // the norm only: it fixes the scale
@@ -1034,14 +1037,15 @@ static void ir_step(Plan &pl) {
     const Lv<double> *L64 = pl.outer64.as<Lv<double>>();
     const Lv<float> *L32 = pl.fine32.as<Lv<float>>();
     check_cuda(launch_ir_update(s, L64, L32, ui, un, pl.scales.as<double>(), pl.active.as<int>(),
-                                2),
+                                2, pl.partials3.as<double>()),
                "ir_update");
     check_cuda(launch_ir_residual(s, L64, L32, ui, un, pl.scales.as<double>() + M,
                                   pl.partials.as<double>(), 0, pl.active.as<int>(), 2,
                                   pl.partials2.as<double>(), pl.maxnz),
                "ir_residual");
     check_cuda(launch_ir_track(s, L64, L32, ui, un, pl.scales.as<double>(), pl.active.as<int>(), M,
-                               pl.maxnz, pl.partials.as<double>(), pl.partials2.as<double>()),
+                               pl.maxnz, pl.partials.as<double>(), pl.partials2.as<double>(),
+                               pl.partials3.as<double>()),
                "ir_track");
     check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>(), M,
                                pl.norms.as<double>(), 1, nullptr, nullptr),
@@ -1049,7 +1053,10 @@ static void ir_step(Plan &pl) {
     check_cuda(launch_finalize(s, pl.partials2.as<double>(), pl.dfirst.as<int>(), M,
                                pl.norms.as<double>() + M, 1, nullptr, nullptr),
                "finalize");
-    count(pl, 5);
+    check_cuda(launch_finalize(s, pl.partials3.as<double>(), pl.dfirst.as<int>(), M,
+                               pl.norms.as<double>() + 2 * M, 1, nullptr, nullptr),
+               "finalize");
+    count(pl, 6);
 }
 
 static void ir_step_graph(Plan &pl) {
@@ -1116,8 +1123,15 @@ void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph) {
     ir_push_state(pl, run);
     if (use_graph) ir_step_graph(pl);
     else ir_step(pl);
-    read_norms(pl, 2 * M);
+    read_norms(pl, 3 * M);
     p0.prof_collect(use_graph);
+    for (int m = 0; m < M; ++m) {
+        MemberRun &r = *run[m];
+        if (!r.active) continue;
+        r.dx_prev = r.dx_last;
+        r.dx_last = pl.host_norms[2 * M + m];
+        if (r.iters == 0) r.dx_first = r.dx_last;
+    }
     // Error bounds of the stored residual.  A tracked member whose bound is
     // not below 0.1% of its residual (or whose residual is not finite) gets
     // the residual recomputed in FP64 -- it replaces the tracked one -- and
@@ -1159,8 +1173,36 @@ void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph) {
     }
 }
 
+// Estimate of ||x* - x|| / ||x*|| for a refinement solve from x = 0.  If the
+// last step contracts the error by q, the error left after its update dx_S is
+// q / (1 - q) ||dx_S||, and ||x*|| is the first update to within the first
+// step's contraction (x = dx_1 after one step).  The last step's error
+// contraction is taken as its residual reduction r_S / r_{S-1}, scaled by how
+// much more the error than the residual contracted in the step before: that
+// step's error contraction is ||dx_S|| / ||dx_{S-1}|| (each update is about
+// the error before its step), its residual reduction r_{S-1} / r_{S-2}.
+// Residuals contract faster than errors, their smooth part being amplified
+// most by A^{-1}, so the residual reduction alone underestimates.  With q
+// near or above 1 (stagnation at the FP64 attainable residual) the last
+// update is taken, times ten.  0 for a zero right-hand side; 1 when no step
+// ran (x = 0).
+static double error_estimate(const MemberRun &r) {
+    if (r.bnorm == 0.0) return 0.0;
+    if (r.hist.size() < 2 || !(r.dx_first > 0)) return 1.0;
+    const size_t S = r.hist.size() - 1;  // steps done; hist[0] = 1
+    double q = r.hist[S] / r.hist[S - 1];
+    if (S >= 2 && r.dx_prev > 0 && r.hist[S - 1] > 0) {
+        const double qe_prev = r.dx_last / r.dx_prev;
+        const double qr_prev = r.hist[S - 1] / r.hist[S - 2];
+        if (qr_prev > 0) q *= std::max(1.0, qe_prev / qr_prev);
+    }
+    const double ratio = r.dx_last / r.dx_first;
+    if (!std::isfinite(q) || !std::isfinite(ratio)) return -1.0;
+    return ratio * (q < 0.9 ? q / (1.0 - q) : 10.0);
+}
+
 ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res) {
-    return finish(r.rel, r.iters, r.rtol, false, res, secs);
+    return finish(r.rel, r.iters, r.rtol, false, res, secs, error_estimate(r));
 }
 
 ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,

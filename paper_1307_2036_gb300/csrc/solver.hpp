@@ -127,9 +127,9 @@ struct Plan {
     int outer_off = 0, outer_n = 0;   // finest columns, lv = member
     int norm_off[2] = {0, 0}, norm_n = 0;  // finest columns, lv = descriptor, u[0] / u[1]
     std::vector<int> outer_first;     // per-member ranges of outer items
-    DevBuf dfirst, partials, partials2, norms, scales, counts, active;
+    DevBuf dfirst, partials, partials2, partials3, norms, scales, counts, active;
     std::vector<int> stage_active;
-    std::vector<double> host_norms;       // [2 M]: norms, then magnitudes
+    std::vector<double> host_norms;       // [3 M]: norms, magnitudes, update norms
     double *hnorms = nullptr;             // mapped pinned staging of the device norms [4 M]
     double *hnorms_dev = nullptr;         // its device address
     size_t hnorms_n = 0;
@@ -204,6 +204,8 @@ struct MemberRun {
     // FP64; errb bounds |tracked - true residual| (2-norm), magx ~ || |A| |x| ||
     int mode = 1;
     double errb = 0.0, magx = 0.0;
+    // norms of the first, the one but last and the latest update of x (error estimate)
+    double dx_first = 0.0, dx_prev = 0.0, dx_last = 0.0;
 };
 
 void ir_bind(Plan &pl, const std::vector<MemberRun *> &run);

@@ -41,7 +41,8 @@ class ellsolve_opts(C.Structure):
 
 
 class ellsolve_result(C.Structure):
-    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("seconds", C.c_double)]
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("seconds", C.c_double),
+                ("rel_error_est", C.c_double)]
 
 
 _vp, _i, _d, _st = C.c_void_p, C.c_int, C.c_double, C.c_int

@@ -94,3 +94,20 @@ def test_mg_beats_cg_and_cg_grows_with_omega(oracle_mod):
     assert out[100.0][0] <= out[1.0][0] + 3
     assert out[100.0][1] >= 3 * out[1.0][1]
     assert out[100.0][0] < out[100.0][1]
+
+
+def test_fp64_attainable_residual_of_strongly_coupled_columns(oracle_mod):
+    """Why some 1e-10 requests end NOT_CONVERGED: on the graded sphere with
+    n_z = 128 and lambda about 4 (serving classes), no FP64 iterate has a
+    relative residual of 1e-10.  The oracle's own FP64 multigrid stagnates
+    above it, and changing its converged iterate by one ulp per entry moves the
+    residual further above it (the residual of any FP64 vector is at least of
+    the size eps ||A|| ||u|| / ||b||)."""
+    og = oracle_mod.Grid(1, 8, 128, inputs.radial_levels(128, graded=True), 0.0514, 4.1 ** 2)
+    b = og.volumes() * inputs.uniform_pm1(og.shape(), member=3)
+    u, it, hist = og.mg_solve(b, rtol=1e-14, maxit=30)
+    assert hist.min() > 1e-10
+    assert abs(hist[-1] - hist[-5]) < 0.1 * hist[-1]  # stagnated, not still converging
+    rng = np.random.default_rng(0)
+    ur = u * (1 + np.finfo(float).eps * rng.uniform(-1, 1, u.shape))
+    assert np.linalg.norm(og.residual(b, ur)) / np.linalg.norm(b) > 1e-10
