@@ -259,6 +259,7 @@ def run_ours(args, rank, world, local_rank):
     stream.synchronize()
     N = sv.N
     tuned_ctas, tuned_ms = sv.autotune()
+    level_shapes = [list(sv.level_tuning(l)) for l in range(sv.nlevels)]
 
     def solve():
         st, res = sv.solve(f, x, rtol=rtol, maxit=60)
@@ -409,6 +410,10 @@ def run_ours(args, rank, world, local_rank):
                        "tracked residual, CUDA graph"),
             "inner_cycles": args.inner_cycles,
             "autotuned_smoother_ctas_per_sm": tuned_ctas,
+            "autotuned_level_shapes": {
+                "fields": "smoother CTAs/SM, ring steps, tmem (0 auto, 1 on, 2 off), "
+                          "restrict chunk blocks, prolong chunk blocks",
+                "levels": level_shapes},
             "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
             "final_rel_residual": final_rel, "time_to_rtol_ms": ms / args.steps,
             "rel_error_est": res.rel_error_est,

@@ -247,21 +247,36 @@ ellsolve_status ellsolve_profile_read(ellsolve_t h, double *smoother_ms_total, i
 uint64_t ellsolve_launch_count(ellsolve_t h);
 
 /* ---- autotuning ----
- * Times the FP32 line smoother on the handle's finest level for each candidate
- * pair (resident CTAs per SM, depth of its shared-memory staging ring) and
- * keeps the fastest for later solves on this handle and for batches led by it.
- * The occupancy cap bounds the L2 working set of the back substitution; the
- * ring depth trades prefetch distance against shared memory per CTA.  The
- * choice changes no result (same arithmetic, different scheduling).  Uses the
- * handle's own FP32 buffers as scratch: call it between solves.  precision 1
- * only.  out_ctas / out_ms (nullable) receive the chosen cap and its time per
- * sweep.  The paper has no counterpart (its kernels are tuned by hand). */
+ * Times, on every level of the handle's hierarchy, the launch shapes of its
+ * kernels and keeps the fastest for later solves on this handle and for
+ * batches led by it: for the FP32 line smoother, the resident CTAs per SM (the
+ * occupancy cap bounds the L2 working set of the back substitution), the depth
+ * of its shared-memory staging ring (prefetch distance against shared memory
+ * per CTA) and whether the eliminated right-hand side is parked in tensor
+ * memory or in the output buffer; for the residual + restriction and the
+ * prolongation of small levels, how far a launch is split along the vertical.
+ * The choice changes no result (same arithmetic, different scheduling).  Uses
+ * the handle's own FP32 buffers as scratch: call it between solves.
+ * precision 1 only.  out_ctas / out_ms (nullable) receive the finest level's
+ * CTA cap and its time per sweep.  The paper has no counterpart (its kernels
+ * are tuned by hand). */
 ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms);
-/* Set or read the two tuning values directly: ctas_per_sm 0..16 (0 = as many
- * as fit), ring 4 or 8 steps; ERR_ARG outside those.  No result depends on
- * them. */
+/* Set the smoother's CTA cap and ring depth on every level, or read the
+ * finest level's: ctas_per_sm 0..16 (0 = as many as fit), ring 4 or 8 steps;
+ * ERR_ARG outside those.  No result depends on them. */
 ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring);
 ellsolve_status ellsolve_get_tuning(ellsolve_t h, int *ctas_per_sm, int *ring);
+/* Set or read one level's launch shape: the smoother's ctas_per_sm (0..16)
+ * and ring (4 or 8), tmem (where the smoother parks its eliminated right-hand
+ * side: 0 tensor memory on launches of at least 152 CTAs, 1 always while
+ * n_z <= 256, 2 never), and the block counts (>= 1) up to which the
+ * restriction from this level and the prolongation onto it are split along
+ * the vertical.  ERR_ARG outside those or for a level the handle lacks.  No
+ * result depends on them. */
+ellsolve_status ellsolve_set_level_tuning(ellsolve_t h, int level, int ctas_per_sm, int ring,
+                                          int tmem, int restrict_chunk, int prolong_chunk);
+ellsolve_status ellsolve_get_level_tuning(ellsolve_t h, int level, int *ctas_per_sm, int *ring,
+                                          int *tmem, int *restrict_chunk, int *prolong_chunk);
 
 /* ---- serving: continuous batching of independent solves ----
  * A server owns one CUDA stream's worth of work; submitted requests are admitted

@@ -1895,31 +1895,33 @@ static cudaError_t launch_tw_zfat(cudaStream_t s, const Lv<float> *L, const Item
 // lengthen a latency-bound sweep.
 template <int Z, int FR, bool ALN>
 static cudaError_t launch_tw_zfa(cudaStream_t s, const Lv<float> *L, const Item *items,
-                                 int nitems, float rho, int max_nz, int ctas_per_sm) {
-    if (max_nz <= kTwTmemMaxNz && nitems >= 152)
+                                 int nitems, float rho, int max_nz, int ctas_per_sm, int tmem) {
+    const bool tm = max_nz <= kTwTmemMaxNz && (tmem == 1 || (tmem == 0 && nitems >= 152));
+    if (tm)
         return launch_tw_zfat<Z, FR, ALN, true>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
     return launch_tw_zfat<Z, FR, ALN, false>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
 }
 
 template <int Z, int FR>
 static cudaError_t launch_tw_zf(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
-                                float rho, int max_nz, int ctas_per_sm, bool aligned) {
-    if (aligned) return launch_tw_zfa<Z, FR, true>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
-    return launch_tw_zfa<Z, FR, false>(s, L, items, nitems, rho, max_nz, ctas_per_sm);
+                                float rho, int max_nz, int ctas_per_sm, bool aligned, int tmem) {
+    if (aligned)
+        return launch_tw_zfa<Z, FR, true>(s, L, items, nitems, rho, max_nz, ctas_per_sm, tmem);
+    return launch_tw_zfa<Z, FR, false>(s, L, items, nitems, rho, max_nz, ctas_per_sm, tmem);
 }
 
 cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                              float rho, int max_nz, int zero_mode, int ctas_per_sm, int ring,
-                             bool aligned) {
+                             bool aligned, int tmem) {
     if (nitems <= 0) return cudaSuccess;
     if (ring == 8) {
         if (zero_mode == 1)
-            return launch_tw_zf<1, 8>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
-        return launch_tw_zf<0, 8>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
+            return launch_tw_zf<1, 8>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
+        return launch_tw_zf<0, 8>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
     }
     if (zero_mode == 1)
-        return launch_tw_zf<1, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
-    return launch_tw_zf<0, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned);
+        return launch_tw_zf<1, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
+    return launch_tw_zf<0, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
 }
 
 bool smooth_tw_fits(int max_nz, int ring) {
@@ -1949,8 +1951,8 @@ cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int 
 // Level chunks for a launch of nitems column blocks: small launches are split
 // along the vertical (chunks of at least 8 levels) until about four blocks per
 // SM exist; large ones run every column whole.
-static int level_chunks(int nitems, int max_nz) {
-    const int want = 4 * 152;
+static int level_chunks(int nitems, int max_nz, int want) {
+    if (want < 1) want = 4 * 152;
     if (nitems >= want || max_nz < 16) return 1;
     const int by_size = (want + nitems - 1) / nitems;
     const int by_depth = max_nz / 8;
@@ -1959,12 +1961,12 @@ static int level_chunks(int nitems, int max_nz) {
 
 template <typename T>
 cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
-                                  int max_nz) {
+                                  int max_nz, int chunk_blocks) {
     if (nitems <= 0) return cudaSuccess;
     const size_t bytes = size_t(restrict_ring<T>()) * 16 * kBlk * sizeof(T);
     cudaError_t e = set_smem(k_restrict_resid<T>, bytes);
     if (e != cudaSuccess) return e;
-    const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz)));
+    const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz, chunk_blocks)));
     k_restrict_resid<T><<<grid, kBlk, bytes, s>>>(L, items);
     return cudaGetLastError();
 }
@@ -1988,9 +1990,9 @@ cudaError_t launch_restrict_rhs(cudaStream_t s, const Lv<T> *L, const Item *item
 
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
-                               int mode, int max_nz) {
+                               int mode, int max_nz, int chunk_blocks) {
     if (nitems <= 0) return cudaSuccess;
-    const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz)));
+    const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz, chunk_blocks)));
     k_prolong_add<T><<<grid, kBlk, 0, s>>>(L, items, mode);
     return cudaGetLastError();
 }
@@ -2140,10 +2142,10 @@ cudaError_t launch_cg_scalars(cudaStream_t s, double *scalars, const double *sum
     template cudaError_t launch_resid<T>(cudaStream_t, const Lv<T> *, const Item *, int, int,    \
                                          double *);                                              \
     template cudaError_t launch_restrict_resid<T>(cudaStream_t, const Lv<T> *, const Item *,     \
-                                                  int, int);                                     \
+                                                  int, int, int);                                \
     template cudaError_t launch_restrict_rhs<T>(cudaStream_t, const Lv<T> *, const Item *, int);  \
     template cudaError_t launch_prolong_add<T>(cudaStream_t, const Lv<T> *, const Item *, int,   \
-                                               int, int);                                        \
+                                               int, int, int);                                   \
     template cudaError_t launch_form_rhs<T>(cudaStream_t, const Lv<T> *, const Item *, int,      \
                                             const double *, T *, double *);
 ELLS_INST(float)

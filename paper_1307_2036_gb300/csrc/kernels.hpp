@@ -20,10 +20,11 @@ cudaError_t launch_smooth(cudaStream_t s, const Lv<T> *L, const Item *items, int
 // ncol % 4 == 0, an even nz with (nz/2) % ring == 0, and zero_mode 0 or 1.
 // ctas_per_sm > 0 caps the resident CTAs per SM (through the shared-memory
 // request); ring is the staging depth (4 or 8 steps); aligned: every level has
-// n % 32 == 0.
+// n % 32 == 0; tmem: f' parked in tensor memory 0 on launches of at least 152
+// CTAs, 1 always, 2 never (in the output buffer); only where max_nz <= 256.
 cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
                              float rho, int max_nz, int zero_mode, int ctas_per_sm, int ring,
-                             bool aligned);
+                             bool aligned, int tmem);
 bool smooth_tw_fits(int max_nz, int ring);
 
 // Whether the generic smoother keeps its Thomas coefficients in the level's
@@ -37,11 +38,12 @@ cudaError_t launch_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int 
                          double *partials);
 
 // b of descriptor lv+1 = 2x2 sums of (b - A u[in]) on descriptor lv.  Items
-// run over the coarse columns; max_nz: the largest nz among them (small
-// launches are split along the vertical).
+// run over the coarse columns; max_nz: the largest nz among them.  Launches of
+// fewer than chunk_blocks blocks are split along the vertical (chunks of at
+// least 8 levels) until about chunk_blocks blocks exist.
 template <typename T>
 cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
-                                  int max_nz);
+                                  int max_nz, int chunk_blocks);
 
 // b of descriptor lv+1 = 2x2 sums of b on descriptor lv (full multigrid).
 // Items run over the coarse columns.
@@ -50,10 +52,10 @@ cudaError_t launch_restrict_rhs(cudaStream_t s, const Lv<T> *L, const Item *item
 
 // u[out] of descriptor lv += P u[in] of descriptor lv+1 (items: fine columns);
 // items flagged zero write P u[in] without reading u[out].  mode 0 bilinear,
-// 1 constant.
+// 1 constant.  chunk_blocks: as for launch_restrict_resid.
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items, int nitems,
-                               int mode, int max_nz);
+                               int mode, int max_nz, int chunk_blocks);
 
 // Iterative-refinement outer step, per member m (items' lv = member index):
 //   r = A_P V_k f - A x   in FP64, f = L64[m].b (pointwise), x = L64[m].u[0],

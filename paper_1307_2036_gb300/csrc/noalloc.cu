@@ -112,7 +112,7 @@ ellsolve_status smooth_static(Problem &p, int level, const void *b, void *u, int
     const int launches = rb ? 2 * nsweeps : nsweeps;
     for (int sw = 0; sw < launches; ++sw)
         launch_smoother<T>(p, s, L, it + size_t(sw & 1) * per, per, rho, p.nz, 0, rows,
-                           p.lev[level].n % 32 == 0);
+                           p.lev[level].n % 32 == 0, level);
     if (launches & 1)
         check_cuda(cudaMemcpyAsync(u, d.u[1], nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                    "copy back");

@@ -209,6 +209,7 @@ void Problem::build(const ellsolve_grid &g, double w2, double l2, const double *
     lev.resize(nlev);
     h64.resize(nlev);
     h32.resize(nlev);
+    shape.assign(nlev, LevelShape{});
     const bool glob32 = smooth_uses_global_scratch(nz, 4);
     for (int l = 0; l < nlev; ++l) {
         const LevelGeom &G = geom->lev[l];
@@ -446,6 +447,7 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
         op.off = int(items.size());
         op.rho = rho;
         op.max_nz = 0;
+        op.tune = ml.front().second;
         int nz_items = 0, z_items = 0;
         op.rows_ok = true;
         op.aligned = true;
@@ -520,6 +522,7 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
     auto emit_prolong = [&](const std::vector<std::pair<int, int>> &up, bool onto_zero) {
         Op op;
         op.kind = Op::kProlong;
+        op.tune = up.empty() ? 0 : up.front().second;
         op.off = int(items.size());
         for (auto [m, l] : up) {
             push_items(items, base[m] + l, mem[m]->lev[l].ncol, st[m].cur[l + 1], st[m].cur[l],
@@ -565,6 +568,7 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
                     Op op;
                     op.kind = Op::kRestrict;
                     op.rows_ok = pass == 0;
+                    op.tune = list.front().second;
                     op.off = int(items.size());
                     for (auto [m, l] : list) {
                         push_items(items, base[m] + l, mem[m]->lev[l + 1].ncol, st[m].cur[l], 0,
@@ -666,20 +670,22 @@ bool rows_eligible(const Problem &p, int level) {
 
 template <typename T>
 void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
-                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned) {
+                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned,
+                     int level) {
     if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
         const Lv<float> *Lf = reinterpret_cast<const Lv<float> *>(L);
-        check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode,
-                                    p.smooth_ctas_per_sm, p.smooth_ring, aligned),
+        const LevelShape &sh = p.level_shape(level);
+        check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode, sh.ctas,
+                                    sh.ring, aligned, sh.tmem),
                    "smooth_tw");
     } else {
         check_cuda(launch_smooth<T>(s, L, it, n, T(rho), max_nz, zero_mode), "smooth");
     }
 }
 template void launch_smoother<float>(const Problem &, cudaStream_t, const Lv<float> *,
-                                     const Item *, int, double, int, int, bool, bool);
+                                     const Item *, int, double, int, int, bool, bool, int);
 template void launch_smoother<double>(const Problem &, cudaStream_t, const Lv<double> *,
-                                      const Item *, int, double, int, int, bool, bool);
+                                      const Item *, int, double, int, int, bool, bool, int);
 static void count(Plan &pl, int n = 1) {
     for (Problem *p : pl.mem) p->launches += uint64_t(n);
 }
@@ -704,7 +710,7 @@ static void run_program(Plan &pl, const Program &prog) {
                 const bool timed = p0.prof && op.finest;
                 if (timed) p0.prof_mark_begin(s);
                 launch_smoother<T>(p0, s, L, it + op.off, op.n, op.rho, op.max_nz, op.zero_mode,
-                                   op.rows_ok, op.aligned);
+                                   op.rows_ok, op.aligned, op.tune);
                 if (timed) p0.prof_mark_end(s, op.bytes);
                 count(pl);
                 break;
@@ -715,7 +721,9 @@ static void run_program(Plan &pl, const Program &prog) {
                                                     it + op.off, op.n),
                                "restrict_rows");
                 else
-                    check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n, pl.maxnz), "restrict");
+                    check_cuda(launch_restrict_resid<T>(s, L, it + op.off, op.n, pl.maxnz,
+                                                        p0.level_shape(op.tune).restrict_chunk),
+                               "restrict");
                 count(pl);
                 break;
             case Op::kRestrictRhs:
@@ -723,7 +731,9 @@ static void run_program(Plan &pl, const Program &prog) {
                 count(pl);
                 break;
             case Op::kProlong:
-                check_cuda(launch_prolong_add<T>(s, L, it + op.off, op.n, o.prolong, pl.maxnz), "prolong");
+                check_cuda(launch_prolong_add<T>(s, L, it + op.off, op.n, o.prolong, pl.maxnz,
+                                                 p0.level_shape(op.tune).prolong_chunk),
+                           "prolong");
                 count(pl);
                 break;
             case Op::kMemset: {
@@ -1302,7 +1312,7 @@ static ellsolve_status solve_pcg(Problem &p, const double *f, double *x, double 
         } else if (ssor) {
             for (int h = 0; h < 4; ++h)
                 launch_smoother<double>(p, s, sdesc.as<Lv<double>>(), sitems.as<Item>() + h * per0,
-                                        per0, 1.0, p.nz, h == 0 ? 1 : 0, false, 0);
+                                        per0, 1.0, p.nz, h == 0 ? 1 : 0, false, false, 0);
             check_cuda(launch_dot(s, L, it, ni, r, z, part), "dot");
             p.launches += 4;
         } else {
@@ -1448,7 +1458,7 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
             const int launches = p.opts.smoother == 1 ? 2 * nsweeps : nsweeps;
             for (int sw = 0; sw < launches; ++sw)
                 launch_smoother<T>(p, s, L, it + sw * per, per, rho, p.nz, 0, rows,
-                                   p.lev[level].n % 32 == 0);
+                                   p.lev[level].n % 32 == 0, level);
             if (launches & 1)
                 check_cuda(cudaMemcpyAsync(out, tmp.p, nl * sizeof(T), cudaMemcpyDeviceToDevice, s),
                            "copy back");
@@ -1460,15 +1470,32 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
                                                 div_up(p.lev[level + 1].ncol, kBlk)),
                            "restrict_rows");
             else
-                check_cuda(launch_restrict_resid<T>(s, L, it, div_up(p.lev[level + 1].ncol, kBlk), p.nz),
+                check_cuda(launch_restrict_resid<T>(s, L, it, div_up(p.lev[level + 1].ncol, kBlk), p.nz,
+                                                    p.level_shape(level).restrict_chunk),
                            "restrict");
             break;
         case 4:
-            check_cuda(launch_prolong_add<T>(s, L, it, per, p.opts.prolong, p.nz), "prolong");
+            check_cuda(launch_prolong_add<T>(s, L, it, per, p.opts.prolong, p.nz,
+                                             p.level_shape(level).prolong_chunk),
+                       "prolong");
             break;
     }
     check_cuda(cudaStreamSynchronize(s), "level op sync");
     return ELLSOLVE_OK;
+}
+
+// Time `run` (one launch sequence) after a warm-up: mean ms of three.
+template <typename F>
+double time_ms(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, F run) {
+    run();
+    check_cuda(cudaEventRecord(e0, s), "record");
+    const int reps = 3;
+    for (int r = 0; r < reps; ++r) run();
+    check_cuda(cudaEventRecord(e1, s), "record");
+    check_cuda(cudaEventSynchronize(e1), "sync");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    return double(ms) / reps;
 }
 
 }  // namespace ells
@@ -1756,55 +1783,119 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
     if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
     if (h->opts.precision != 1) throw Error(ELLSOLVE_ERR_ARG, "autotune needs precision 1");
     cudaStream_t s = h->stream;
-    const LevelStore &L0 = h->lev[0];
-    const size_t nl = size_t(L0.ncol) * h->nz;
-    const bool rows = rows_eligible(*h, 0);
-    // one smoother sweep on level 0 of the handle's own buffers (zeroed)
-    check_cuda(cudaMemsetAsync(L0.u32[0].p, 0, nl * 4, s), "zero");
-    check_cuda(cudaMemsetAsync(L0.b32.p, 0, nl * 4, s), "zero");
-    std::vector<Lv<float>> hd{h->h32[0]};
-    std::vector<Item> items;
-    push_items(items, 0, L0.ncol, 0, 1, 0);
-    DevBuf dd, di;
-    upload(dd, hd, s);
-    upload(di, items, s);
     cudaEvent_t e0, e1;
     check_cuda(cudaEventCreate(&e0), "event");
     check_cuda(cudaEventCreate(&e1), "event");
-    // (resident CTAs per SM, ring depth) candidates of the smoother in use
-    const std::vector<std::pair<int, int>> candidates = {{3, 8}, {4, 8}, {5, 8},
-                                                         {3, 4}, {4, 4}, {5, 4}};
-    int best = h->smooth_ctas_per_sm, best_ring = h->smooth_ring;
-    double best_ms = 1e300;
-    const int keep = h->smooth_ctas_per_sm, keep_ring = h->smooth_ring;
-    for (auto [ctas, ring] : candidates) {
-        h->smooth_ctas_per_sm = ctas;
-        h->smooth_ring = ring;
-        auto sweep = [&]() {
-            launch_smoother<float>(*h, s, dd.as<Lv<float>>(), di.as<Item>(), int(items.size()), 0.8,
-                                   h->nz, 0, rows, L0.n % 32 == 0);
-        };
-        sweep();  // warm-up
-        check_cuda(cudaEventRecord(e0, s), "record");
-        const int reps = 3;
-        for (int r = 0; r < reps; ++r) sweep();
-        check_cuda(cudaEventRecord(e1, s), "record");
-        check_cuda(cudaEventSynchronize(e1), "sync");
-        float ms = 0.f;
-        check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
-        if (ms / reps < best_ms) {
-            best_ms = ms / reps;
-            best = ctas;
-            best_ring = ring;
+    double ms0 = 0.0;
+    try {
+        for (int l = 0; l < h->nlev; ++l) {
+            using ells::time_ms;
+            const LevelStore &Ls = h->lev[l];
+            const size_t nl = size_t(Ls.ncol) * h->nz;
+            const int nitems = div_up(Ls.ncol, kBlk);
+            // the level's own FP32 buffers as scratch (zeroed)
+            check_cuda(cudaMemsetAsync(Ls.u32[0].p, 0, nl * 4, s), "zero");
+            check_cuda(cudaMemsetAsync(Ls.u32[1].p, 0, nl * 4, s), "zero");
+            check_cuda(cudaMemsetAsync(Ls.b32.p, 0, nl * 4, s), "zero");
+            std::vector<Lv<float>> hd{h->h32[l]};
+            if (l + 1 < h->nlev) hd.push_back(h->h32[l + 1]);
+            std::vector<Item> items;
+            push_items(items, 0, Ls.ncol, 0, 1, 0);
+            const int off_c = int(items.size());
+            if (l + 1 < h->nlev) push_items(items, 0, h->lev[l + 1].ncol, 0, 0, 0);
+            DevBuf dd, di;
+            upload(dd, hd, s);
+            upload(di, items, s);
+            LevelShape &sh = h->shape[size_t(l)];
+            // (a) the line smoother: resident CTAs per SM, ring depth and where
+            // f' is parked, on the levels the twisted kernel takes
+            if (rows_eligible(*h, l)) {
+                std::vector<LevelShape> cand;
+                const bool tm_ok = h->nz <= 256;
+                if (nitems >= 152) {
+                    for (int c : {3, 4, 5}) cand.push_back({c, 8, 0});
+                    cand.push_back({4, 4, 0});
+                    for (int c : {4, 5}) cand.push_back({c, 8, 2});
+                    cand.push_back({5, 4, 2});
+                } else {
+                    cand.push_back({4, 8, 2});
+                    cand.push_back({4, 4, 2});
+                    if (tm_ok) cand.push_back({4, 8, 1});
+                }
+                double best = 1e300;
+                LevelShape keep = sh;
+                for (const LevelShape &c : cand) {
+                    sh.ctas = c.ctas;
+                    sh.ring = c.ring;
+                    sh.tmem = c.tmem;
+                    const double ms = time_ms(s, e0, e1, [&] {
+                        launch_smoother<float>(*h, s, dd.as<Lv<float>>(), di.as<Item>(), nitems,
+                                               0.8, h->nz, 0, true, Ls.n % 32 == 0, l);
+                    });
+                    if (ms < best) {
+                        best = ms;
+                        keep = sh;
+                    }
+                }
+                sh.ctas = keep.ctas;
+                sh.ring = keep.ring;
+                sh.tmem = keep.tmem;
+                if (l == 0) ms0 = best;
+            }
+            // (b) the transfers of small levels: how far to split them along
+            // the vertical (the row-staged restriction of large levels is not
+            // split)
+            if (l + 1 < h->nlev) {
+                const int nc_items = div_up(h->lev[l + 1].ncol, kBlk);
+                const bool rows_r = restrict_rows_eligible(*h, l) && restrict_rows_preferred(*h, l);
+                if (!rows_r && nc_items < 4 * 152) {
+                    double best = 1e300;
+                    int keep = sh.restrict_chunk;
+                    for (int want : {152, 304, 608, 1216}) {
+                        const double ms = time_ms(s, e0, e1, [&] {
+                            check_cuda(launch_restrict_resid<float>(s, dd.as<Lv<float>>(),
+                                                                    di.as<Item>() + off_c,
+                                                                    nc_items, h->nz, want),
+                                       "restrict");
+                        });
+                        if (ms < best) {
+                            best = ms;
+                            keep = want;
+                        }
+                    }
+                    sh.restrict_chunk = keep;
+                }
+                if (nitems < 4 * 152) {
+                    double best = 1e300;
+                    int keep = sh.prolong_chunk;
+                    for (int want : {152, 304, 608, 1216}) {
+                        const double ms = time_ms(s, e0, e1, [&] {
+                            check_cuda(launch_prolong_add<float>(s, dd.as<Lv<float>>(),
+                                                                 di.as<Item>(), nitems,
+                                                                 h->opts.prolong, h->nz, want),
+                                       "prolong");
+                        });
+                        if (ms < best) {
+                            best = ms;
+                            keep = want;
+                        }
+                    }
+                    sh.prolong_chunk = keep;
+                }
+            }
+            check_cuda(cudaStreamSynchronize(s), "autotune sync");
         }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->smooth_ctas_per_sm = rows ? best : keep;
-    h->smooth_ring = rows ? best_ring : keep_ring;
     if (h->plan) h->plan->drop_graph();
-    if (out_ctas) *out_ctas = h->smooth_ctas_per_sm;
-    if (out_ms) *out_ms = best_ms;
+    if (h->batch_plan) h->batch_plan->drop_graph();
+    if (out_ctas) *out_ctas = h->shape[0].ctas;
+    if (out_ms) *out_ms = ms0;
     return ELLSOLVE_OK;
     ELLS_GUARD_END
 }
@@ -1829,8 +1920,10 @@ ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring) {
     if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
     if (ctas_per_sm < 0 || ctas_per_sm > 16) throw Error(ELLSOLVE_ERR_ARG, "ctas_per_sm must be 0..16");
     if (ring != 4 && ring != 8) throw Error(ELLSOLVE_ERR_ARG, "ring must be 4 or 8");
-    h->smooth_ctas_per_sm = ctas_per_sm;
-    h->smooth_ring = ring;
+    for (LevelShape &sh : h->shape) {
+        sh.ctas = ctas_per_sm;
+        sh.ring = ring;
+    }
     if (h->plan) h->plan->drop_graph();
     return ELLSOLVE_OK;
     ELLS_GUARD_END
@@ -1839,11 +1932,44 @@ ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring) {
 ellsolve_status ellsolve_get_tuning(ellsolve_t h, int *ctas_per_sm, int *ring) {
     ELLS_GUARD_BEGIN
     if (!h) throw Error(ELLSOLVE_ERR_ARG, "null handle");
-    if (ctas_per_sm) *ctas_per_sm = h->smooth_ctas_per_sm;
-    if (ring) *ring = h->smooth_ring;
+    if (ctas_per_sm) *ctas_per_sm = h->shape[0].ctas;
+    if (ring) *ring = h->shape[0].ring;
     return ELLSOLVE_OK;
     ELLS_GUARD_END
 }
 
+ellsolve_status ellsolve_set_level_tuning(ellsolve_t h, int level, int ctas_per_sm, int ring,
+                                          int tmem, int restrict_chunk, int prolong_chunk) {
+    ELLS_GUARD_BEGIN
+    if (!h || level < 0 || level >= h->nlev) throw Error(ELLSOLVE_ERR_ARG, "bad handle or level");
+    if (ctas_per_sm < 0 || ctas_per_sm > 16) throw Error(ELLSOLVE_ERR_ARG, "ctas_per_sm must be 0..16");
+    if (ring != 4 && ring != 8) throw Error(ELLSOLVE_ERR_ARG, "ring must be 4 or 8");
+    if (tmem < 0 || tmem > 2) throw Error(ELLSOLVE_ERR_ARG, "tmem must be 0, 1 or 2");
+    if (restrict_chunk < 1 || prolong_chunk < 1)
+        throw Error(ELLSOLVE_ERR_ARG, "chunk targets must be >= 1");
+    LevelShape &sh = h->shape[size_t(level)];
+    sh.ctas = ctas_per_sm;
+    sh.ring = ring;
+    sh.tmem = tmem;
+    sh.restrict_chunk = restrict_chunk;
+    sh.prolong_chunk = prolong_chunk;
+    if (h->plan) h->plan->drop_graph();
+    return ELLSOLVE_OK;
+    ELLS_GUARD_END
+}
+
+ellsolve_status ellsolve_get_level_tuning(ellsolve_t h, int level, int *ctas_per_sm, int *ring,
+                                          int *tmem, int *restrict_chunk, int *prolong_chunk) {
+    ELLS_GUARD_BEGIN
+    if (!h || level < 0 || level >= h->nlev) throw Error(ELLSOLVE_ERR_ARG, "bad handle or level");
+    const LevelShape &sh = h->shape[size_t(level)];
+    if (ctas_per_sm) *ctas_per_sm = sh.ctas;
+    if (ring) *ring = sh.ring;
+    if (tmem) *tmem = sh.tmem;
+    if (restrict_chunk) *restrict_chunk = sh.restrict_chunk;
+    if (prolong_chunk) *prolong_chunk = sh.prolong_chunk;
+    return ELLSOLVE_OK;
+    ELLS_GUARD_END
+}
 
 }  // extern "C"

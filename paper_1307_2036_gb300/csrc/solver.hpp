@@ -71,6 +71,18 @@ struct Geometry {
 std::shared_ptr<const Geometry> geometry_for(const ellsolve_grid &g, int coarsest_min,
                                              int max_levels, cudaStream_t s);
 
+// Launch shape of one level's kernels.  No result depends on it: the same
+// arithmetic runs in another schedule.
+struct LevelShape {
+    int ctas = 3;   // twisted smoother: resident CTAs per SM cap (0: as many as fit)
+    int ring = 8;   // twisted smoother: staging ring depth, 4 or 8 steps
+    int tmem = 0;   // twisted smoother: f' in tensor memory 0 on launches of >= 152
+                    // CTAs, 1 always (n_z <= 256), 2 never
+    int restrict_chunk = 608;  // residual + restriction from this level, and the
+    int prolong_chunk = 608;   // prolongation onto it: launches of fewer blocks are split
+                               // along the vertical until about this many exist
+};
+
 // Device vectors of one multigrid level of one problem.
 struct LevelStore {
     int n = 0, ncol = 0;
@@ -94,6 +106,7 @@ struct Op {
     int zero_mode = 0;        // smoother items: 0 none / 1 all start from zero, 2 mixed
     bool rows_ok = false;     // every level in the op suits the row-staged FP32 smoother
     bool aligned = false;     // every level in the op has n % 32 == 0
+    int tune = 0;             // level whose launch shape the op takes (its first item's)
     int member = 0, level = 0, buf = 0;  // kMemset target
 };
 
@@ -167,8 +180,10 @@ struct Problem {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_graph;
     int ev_next = 0, ev_graph_used = 0;
-    int smooth_ctas_per_sm = 3;  // twisted smoother's occupancy cap (0: as many as fit)
-    int smooth_ring = 8;         // twisted smoother's staging ring depth (4 or 8 steps)
+    std::vector<LevelShape> shape;  // launch shape per level (set by the autotuner)
+    const LevelShape &level_shape(int level) const {
+        return shape[size_t(level < nlev ? level : nlev - 1)];
+    }
     double prof_ms = 0.0, prof_bytes = 0.0;
     long prof_count = 0;
     std::vector<double> ev_free_bytes, ev_graph_bytes;  // bytes per recorded pair
@@ -213,11 +228,12 @@ void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep
 void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph);
 ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res);
 
-// One line-smoother launch: the row-staged FP32 kernels where `rows_ok`, else
-// the generic kernel.
+// One line-smoother launch: the twisted FP32 kernel where `rows_ok`, else the
+// generic kernel; `level`: whose launch shape to take.
 template <typename T>
 void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
-                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned);
+                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned,
+                     int level);
 bool rows_eligible(const Problem &p, int level);
 bool restrict_rows_eligible(const Problem &p, int level);
 bool restrict_rows_preferred(const Problem &p, int level);

@@ -302,8 +302,9 @@ def test_batch_matches_the_oracle(torch_mod, oracle_mod):
 
 
 def test_autotune_changes_no_result(torch_mod, oracle_mod):
-    """ellsolve_autotune only changes the smoother's occupancy cap: a solve
-    before and after tuning gives the same bits."""
+    """ellsolve_autotune only changes launch shapes (per level: the smoother's
+    occupancy cap, ring depth and tensor-memory use, the transfers' vertical
+    split): a solve before and after tuning gives the same bits."""
     from paper_1307_2036_gb300 import ellsolve
     torch = torch_mod
     sv = ellsolve.Solver(1, 32, 32, inputs.radial_levels(32, graded=True), 0.01, 1.0, precision=1)
@@ -312,6 +313,37 @@ def test_autotune_changes_no_result(torch_mod, oracle_mod):
     sv.solve(f, x1, rtol=1e-9, maxit=40)
     ctas, ms = sv.autotune()
     assert 2 <= ctas <= 6 and ms > 0
+    for level in range(sv.nlevels):
+        c, ring, tmem, rc, pc = sv.level_tuning(level)
+        print(f"level {level}: ctas {c} ring {ring} tmem {tmem} restrict chunk {rc} prolong chunk {pc}")
+        assert 0 <= c <= 16 and ring in (4, 8) and tmem in (0, 1, 2) and rc >= 1 and pc >= 1
     sv.solve(f, x2, rtol=1e-9, maxit=40)
     torch.cuda.synchronize()
     assert torch.equal(x1, x2)
+
+
+SHAPES = [  # (ctas per SM, ring, tmem, restrict chunk, prolong chunk) on every level
+    (3, 8, 0, 608, 608), (5, 4, 2, 152, 152), (4, 8, 1, 1216, 1216), (4, 4, 1, 304, 304),
+    (0, 8, 2, 1, 1),
+]
+
+
+@pytest.mark.parametrize("kind,n,nz", [(1, 64, 32), (0, 128, 16), (1, 48, 32)])
+def test_every_launch_shape_gives_the_same_bits(torch_mod, oracle_mod, kind, n, nz):
+    """Each candidate the autotuner may choose, set on every level, gives a
+    solve bit-identical to the default shapes (levels with >= 152 blocks of 128
+    columns, the tensor-memory switch forced both ways, n % 32 == 0 and not)."""
+    from paper_1307_2036_gb300 import ellsolve
+    torch = torch_mod
+    sv = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=True), 0.02, 2.0,
+                         precision=1)
+    f = torch.tensor(inputs.uniform_pm1(sv.shape(), member=19), device="cuda")
+    ref = torch.zeros_like(f)
+    sv.solve(f, ref, rtol=1e-9, maxit=40)
+    for shape in SHAPES:
+        for level in range(sv.nlevels):
+            sv.set_level_tuning(level, *shape)
+        x = torch.zeros_like(f)
+        sv.solve(f, x, rtol=1e-9, maxit=40)
+        torch.cuda.synchronize()
+        assert torch.equal(x, ref), shape
