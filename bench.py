@@ -411,8 +411,8 @@ def run_ours(args, rank, world, local_rank):
             "inner_cycles": args.inner_cycles,
             "autotuned_smoother_ctas_per_sm": tuned_ctas,
             "autotuned_level_shapes": {
-                "fields": "smoother CTAs/SM, ring steps, tmem (0 auto, 1 on, 2 off), "
-                          "restrict chunk blocks, prolong chunk blocks",
+                "fields": "smoother CTAs/SM, ring steps, tmem (0 auto, 1 on, 2 off), staged "
+                          "(0 auto, 1 on, 2 off), restrict chunk blocks, prolong chunk blocks",
                 "levels": level_shapes},
             "rtol": rtol, "vcycles_per_solve": vcycles_per_solve,
             "final_rel_residual": final_rel, "time_to_rtol_ms": ms / args.steps,

@@ -266,17 +266,21 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms);
  * ERR_ARG outside those.  No result depends on them. */
 ellsolve_status ellsolve_set_tuning(ellsolve_t h, int ctas_per_sm, int ring);
 ellsolve_status ellsolve_get_tuning(ellsolve_t h, int *ctas_per_sm, int *ring);
-/* Set or read one level's launch shape: the smoother's ctas_per_sm (0..16)
- * and ring (4 or 8), tmem (where the smoother parks its eliminated right-hand
+/* Set or read one level's launch shape: the streaming smoother's ctas_per_sm
+ * (0..16) and ring (4 or 8), tmem (where it parks its eliminated right-hand
  * side: 0 tensor memory on launches of at least 152 CTAs, 1 always while
- * n_z <= 256, 2 never), and the block counts (>= 1) up to which the
- * restriction from this level and the prolongation onto it are split along
- * the vertical.  ERR_ARG outside those or for a level the handle lacks.  No
- * result depends on them. */
+ * n_z <= 256, 2 never), staged (the fully staged smoother, which copies every
+ * level into shared memory first: 0 on launches of fewer than 152 blocks of
+ * 128 columns, 1 always, 2 never; where n_z % 16 == 0 and n_z <= 256), and the
+ * block counts (>= 1) up to which the restriction from this level and the
+ * prolongation onto it are split along the vertical.  ERR_ARG outside those
+ * or for a level the handle lacks.  No result depends on them. */
 ellsolve_status ellsolve_set_level_tuning(ellsolve_t h, int level, int ctas_per_sm, int ring,
-                                          int tmem, int restrict_chunk, int prolong_chunk);
+                                          int tmem, int staged, int restrict_chunk,
+                                          int prolong_chunk);
 ellsolve_status ellsolve_get_level_tuning(ellsolve_t h, int level, int *ctas_per_sm, int *ring,
-                                          int *tmem, int *restrict_chunk, int *prolong_chunk);
+                                          int *tmem, int *staged, int *restrict_chunk,
+                                          int *prolong_chunk);
 
 /* ---- serving: continuous batching of independent solves ----
  * A server owns one CUDA stream's worth of work; submitted requests are admitted

@@ -823,6 +823,187 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Line smoother for small launches (fewer blocks than SMs), fully staged.  The
+// same twisted elimination and arithmetic as k_smooth_tw, one column per
+// thread with the two halves as the lanes of FP32x2 arithmetic, but a CTA is
+// one warp (32 columns) and copies every level it needs -- the own rows with a
+// halo column each side, b, rows j-1 and j+1 (34 aligned 16-byte chunks per
+// level), and the neighbours off the staged rows into separate arrays -- into
+// shared memory before it starts.  The elimination and the back substitution
+// then run with no barrier or copy wait inside their loops, so the loads of
+// later steps are issued early; f' and c' of every step are parked in tensor
+// memory (2 columns per step each).  A small launch is bound by the latency of
+// the column's sequential sweep, which this shortens; a large one by memory,
+// where the streaming ring of k_smooth_tw is the right design.
+// ---------------------------------------------------------------------------
+constexpr int kStgF = 136;  // floats per staged level: [own 40][b 32][j-1 32][j+1 32]
+
+__host__ __device__ inline size_t stg_smem_bytes(int max_nz) {
+    return size_t(max_nz) * kStgF * 4 +   // staged rows
+           size_t(max_nz) * 2 * 32 * 4 +  // off-row neighbours: horizontal, vertical
+           size_t(max_nz / 2) * 16 +      // (V_k, V_k'), (g_{k+1}, g_k')
+           16;                            // TMEM base address
+}
+// TMEM columns of a CTA: f' in [0, C), c' in [C, 2C), C a power of two >= max_nz
+__host__ __device__ inline int stg_tmem_half(int max_nz) { return tw_tmem_cols(max_nz); }
+
+template <int ZERO>
+__global__ void __launch_bounds__(32) k_smooth_stg(const Lv<float> *__restrict__ L,
+                                                   const Item *__restrict__ items, float rho,
+                                                   int max_nz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *stg = reinterpret_cast<float *>(smem_raw);
+    float *hb = stg + size_t(max_nz) * kStgF;  // [level][lane]
+    float *vb = hb + size_t(max_nz) * 32;       // [level][lane]
+    float2 *VP = reinterpret_cast<float2 *>(vb + size_t(max_nz) * 32);
+    float2 *GH = VP + max_nz / 2;
+    unsigned *tm_sh = reinterpret_cast<unsigned *>(GH + max_nz / 2);
+    const Item it = items[blockIdx.x >> 2];
+    const Lv<float> &d = L[it.lv];
+    const int nc = d.ncol, nz = d.nz, n = d.n, m = nz / 2;
+    const int lane = threadIdx.x;
+    const int c0w = it.col0 + 32 * int(blockIdx.x & 3);
+    const int c = c0w + lane;
+    const bool active = c < nc;
+    const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
+    constexpr bool zero = ZERO == 1;
+    const unsigned half = unsigned(stg_tmem_half(max_nz));
+    tm_alloc(tm_sh, 2u * half);
+    const float *__restrict__ u = d.u[it.in];
+    float *__restrict__ un = d.u[it.out];
+    const float *__restrict__ b = d.b;
+    const size_t snc = size_t(nc);
+
+    float A = 1.f, sv = 1.f;
+    float2 t0 = f2(0.f), t1 = f2(0.f), t2 = f2(0.f), t3 = f2(0.f);
+    int hd = -1, vd = -1, hc = 0, vc = 0;
+    if (active) {
+        const Column<float> k0 = load_column(d, c);
+        A = k0.A;
+        sv = k0.s;
+        t0 = f2(k0.t0);
+        t1 = f2(k0.t1);
+        t2 = f2(k0.t2);
+        t3 = f2(k0.t3);
+        if (!zero) {
+            const int4 nbr = k0.nb;
+            if (nbr.x != c - 1) { hd = 0; hc = nbr.x; }
+            if (nbr.y != c + 1) { hd = 1; hc = nbr.y; }
+            if (nbr.z != c - n) { vd = 2; vc = nbr.z; }
+            if (nbr.w != c + n) { vd = 3; vc = nbr.w; }
+        }
+    }
+    // staging: lane l copies chunk l (and lanes 0, 1 chunks 32, 33) of every
+    // level; chunk r: 0..9 own row c0w-4.., 10..17 b, 18..25 row j-1, 26..33 row j+1
+    for (int r = lane; r < 34; r += 32) {
+        const float *base;
+        int scol, dst;
+        bool use;
+        if (r < 10) { base = u; scol = c0w - 4 + 4 * r; dst = kOwnT + 4 * r; use = !zero; }
+        else if (r < 18) { base = b; scol = c0w + 4 * (r - 10); dst = kBT + 4 * (r - 10); use = true; }
+        else if (r < 26) { base = u; scol = c0w - n + 4 * (r - 18); dst = kJmT + 4 * (r - 18); use = !zero; }
+        else { base = u; scol = c0w + n + 4 * (r - 26); dst = kJpT + 4 * (r - 26); use = !zero; }
+        if (use && scol >= 0 && scol + 4 <= nc)
+            for (int k = 0; k < nz; ++k) cp_async16(stg + k * kStgF + dst, base + k * snc + scol, 16);
+    }
+    if (hd >= 0)
+        for (int k = 0; k < nz; ++k) cp_async(hb + k * 32 + lane, u + k * snc + hc, true);
+    if (vd >= 0)
+        for (int k = 0; k < nz; ++k) cp_async(vb + k * 32 + lane, u + k * snc + vc, true);
+    cp_async_commit();
+    for (int i = lane; i < m; i += 32) {
+        VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
+        GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
+    }
+    cp_async_wait<0>();
+    tm_fence_before();
+    __syncwarp();
+    tm_fence_after();
+    const unsigned tm = *tm_sh;
+    const int own = kOwnT + 4 + lane;
+
+    float2 u0 = f2(0.f), um = f2(0.f);
+    if (!zero) u0 = make_float2(stg[own], stg[(nz - 1) * kStgF + own]);
+    float2 ratio = f2(0.f), fp = f2(0.f), lo = f2(0.f), lo_g = f2(0.f);
+    Piv2 pv;
+    pv.cp = pv.inv = pv.ratio_next = f2(0.f);
+#pragma unroll 4
+    for (int s = 0; s < m; ++s) {
+        const float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
+        float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
+        const float2 hi_g = GH[s], Vp = VP[s];
+        if (!zero) {
+            // the next level of each half; at the meeting step the other half's
+            const float2 up = s == m - 1 ? make_float2(lt[own], lk[own])
+                                         : make_float2(lk[kStgF + own], lt[own - kStgF]);
+            float2 nw = make_float2(lk[own - 1], lt[own - 1]);
+            float2 ne = make_float2(lk[own + 1], lt[own + 1]);
+            float2 ns = make_float2(lk[kJmT + lane], lt[kJmT + lane]);
+            float2 nn = make_float2(lk[kJpT + lane], lt[kJpT + lane]);
+            if (hd >= 0 || vd >= 0) {
+                const float2 vh = make_float2(hb[s * 32 + lane], hb[(nz - 1 - s) * 32 + lane]);
+                const float2 vv = make_float2(vb[s * 32 + lane], vb[(nz - 1 - s) * 32 + lane]);
+                nw = hd == 0 ? vh : nw;
+                ne = hd == 1 ? vh : ne;
+                ns = vd == 2 ? vv : ns;
+                nn = vd == 3 ? vv : nn;
+            }
+            float2 horiz = __fmul2_rn(t0, sub2(u0, nw));
+            horiz = __ffma2_rn(t1, sub2(u0, ne), horiz);
+            horiz = __ffma2_rn(t2, sub2(u0, ns), horiz);
+            horiz = __ffma2_rn(t3, sub2(u0, nn), horiz);
+            float2 vert = __fmul2_rn(hi_g, sub2(u0, up));
+            vert = __ffma2_rn(lo_g, sub2(u0, um), vert);
+            float2 Au = __fmul2_rn(f2(A), __fmul2_rn(Vp, u0));
+            Au = __ffma2_rn(Vp, horiz, Au);
+            Au = __ffma2_rn(f2(A), vert, Au);
+            r = sub2(r, Au);
+            um = u0;
+            u0 = up;
+        }
+        const float2 hi = __fmul2_rn(f2(A), hi_g);
+        pv = pivot2(__fmul2_rn(Vp, f2(sv)), lo, hi, ratio);
+        fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
+        tm_st2(tm + 2u * unsigned(s), fp);
+        tm_st2(tm + half + 2u * unsigned(s), pv.cp);
+        ratio = pv.ratio_next;
+        lo = hi;
+        lo_g = hi_g;
+    }
+    // meeting of the halves: x_{m-1} and x_m from the two last equations
+    float2 x;
+    {
+        const float den = __fmaf_rn(pv.cp.x, pv.ratio_next.y, pv.ratio_next.x);
+        const float xb = __fmul_rn(__fmaf_rn(pv.cp.x, fp.y, fp.x), rcp(den));
+        x = make_float2(xb, __fmaf_rn(pv.cp.y, xb, fp.y));
+    }
+    tm_wait_st();
+    // back substitution, step s = m-1 .. 0, eight steps per tensor-memory load
+    for (int kb = m / 8 - 1; kb >= 0; --kb) {
+        unsigned fv[16], cv[16];
+        tm_ld<8>(tm + 2u * unsigned(kb * 8), fv);
+        tm_ld<8>(tm + half + 2u * unsigned(kb * 8), cv);
+#pragma unroll
+        for (int jj = 7; jj >= 0; --jj) {
+            const int s = kb * 8 + jj;
+            const float2 fk = make_float2(__uint_as_float(fv[2 * jj]), __uint_as_float(fv[2 * jj + 1]));
+            const float2 ck = make_float2(__uint_as_float(cv[2 * jj]), __uint_as_float(cv[2 * jj + 1]));
+            const float2 uo = zero ? f2(0.f)
+                                   : make_float2(stg[s * kStgF + own], stg[(nz - 1 - s) * kStgF + own]);
+            if (s != m - 1) x = __ffma2_rn(ck, x, fk);
+            const float2 un2 = __ffma2_rn(f2(rho), x, uo);
+            if (active) {
+                __stcs(un + size_t(s) * snc + c, upd ? un2.x : uo.x);
+                __stcs(un + size_t(nz - 1 - s) * snc + c, upd ? un2.y : uo.y);
+            }
+        }
+    }
+    tm_fence_before();
+    __syncwarp();
+    tm_dealloc(tm, 2u * half);
+}
+
+// ---------------------------------------------------------------------------
 // Residual / apply (Sec. 3.1 stencil).
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
@@ -1922,6 +2103,32 @@ cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *ite
     if (zero_mode == 1)
         return launch_tw_zf<1, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
     return launch_tw_zf<0, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
+}
+
+bool smooth_stg_fits(int max_nz) {
+    return max_nz % 16 == 0 && max_nz <= kTwTmemMaxNz && stg_smem_bytes(max_nz) <= kSmemCap;
+}
+
+template <int Z>
+static cudaError_t launch_stg_z(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                                float rho, int max_nz) {
+    size_t bytes = stg_smem_bytes(max_nz);
+    // at most 512 / (tensor-memory columns per CTA) CTAs on an SM, so that the
+    // allocation never waits: the shared memory each CTA takes keeps the rest off
+    const int lim = 512 / (2 * stg_tmem_half(max_nz));
+    const size_t cap = (size_t(228) * 1024) / size_t(lim) - 1024;
+    if (cap > bytes) bytes = cap;
+    cudaError_t e = set_smem(k_smooth_stg<Z>, bytes);
+    if (e != cudaSuccess) return e;
+    k_smooth_stg<Z><<<unsigned(nitems) * 4u, 32, bytes, s>>>(L, items, rho, max_nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_stg(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                              float rho, int max_nz, int zero_mode) {
+    if (nitems <= 0) return cudaSuccess;
+    if (zero_mode == 1) return launch_stg_z<1>(s, L, items, nitems, rho, max_nz);
+    return launch_stg_z<0>(s, L, items, nitems, rho, max_nz);
 }
 
 bool smooth_tw_fits(int max_nz, int ring) {

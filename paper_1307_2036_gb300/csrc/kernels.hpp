@@ -27,6 +27,15 @@ cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *ite
                              bool aligned, int tmem);
 bool smooth_tw_fits(int max_nz, int ring);
 
+// The same sweep for small launches, fully staged: one warp per 32 columns
+// copies every level it needs into shared memory before it starts and parks
+// f' and c' in tensor memory; valid where the twisted kernel is and
+// smooth_stg_fits(max_nz) (n_z % 16 == 0, n_z <= 256).  Bit-identical to
+// launch_smooth_tw.
+cudaError_t launch_smooth_stg(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                              float rho, int max_nz, int zero_mode);
+bool smooth_stg_fits(int max_nz);
+
 // Whether the generic smoother keeps its Thomas coefficients in the level's
 // aux buffer (true) or in shared memory, for a largest nz of max_nz.
 bool smooth_uses_global_scratch(int max_nz, size_t elem_bytes);

@@ -675,9 +675,14 @@ void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Ite
     if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
         const Lv<float> *Lf = reinterpret_cast<const Lv<float> *>(L);
         const LevelShape &sh = p.level_shape(level);
-        check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode, sh.ctas,
-                                    sh.ring, aligned, sh.tmem),
-                   "smooth_tw");
+        const bool stg = smooth_stg_fits(max_nz) && (sh.staged == 1 || (sh.staged == 0 && n < 152));
+        if (stg)
+            check_cuda(launch_smooth_stg(s, Lf, it, n, float(rho), max_nz, zero_mode),
+                       "smooth_stg");
+        else
+            check_cuda(launch_smooth_tw(s, Lf, it, n, float(rho), max_nz, zero_mode, sh.ctas,
+                                        sh.ring, aligned, sh.tmem),
+                       "smooth_tw");
     } else {
         check_cuda(launch_smooth<T>(s, L, it, n, T(rho), max_nz, zero_mode), "smooth");
     }
@@ -1810,17 +1815,20 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
             // (a) the line smoother: resident CTAs per SM, ring depth and where
             // f' is parked, on the levels the twisted kernel takes
             if (rows_eligible(*h, l)) {
-                std::vector<LevelShape> cand;
+                std::vector<LevelShape> cand;  // (ctas, ring, tmem, staged)
                 const bool tm_ok = h->nz <= 256;
+                const bool stg_ok = smooth_stg_fits(h->nz);
                 if (nitems >= 152) {
-                    for (int c : {3, 4, 5}) cand.push_back({c, 8, 0});
-                    cand.push_back({4, 4, 0});
-                    for (int c : {4, 5}) cand.push_back({c, 8, 2});
-                    cand.push_back({5, 4, 2});
+                    for (int c : {3, 4, 5}) cand.push_back({c, 8, 0, 2});
+                    cand.push_back({4, 4, 0, 2});
+                    for (int c : {4, 5}) cand.push_back({c, 8, 2, 2});
+                    cand.push_back({5, 4, 2, 2});
+                    if (stg_ok && nitems < 4 * 152) cand.push_back({4, 8, 0, 1});
                 } else {
-                    cand.push_back({4, 8, 2});
-                    cand.push_back({4, 4, 2});
-                    if (tm_ok) cand.push_back({4, 8, 1});
+                    if (stg_ok) cand.push_back({4, 8, 0, 1});
+                    cand.push_back({4, 8, 2, 2});
+                    cand.push_back({4, 4, 2, 2});
+                    if (tm_ok) cand.push_back({4, 8, 1, 2});
                 }
                 double best = 1e300;
                 LevelShape keep = sh;
@@ -1828,6 +1836,7 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
                     sh.ctas = c.ctas;
                     sh.ring = c.ring;
                     sh.tmem = c.tmem;
+                    sh.staged = c.staged;
                     const double ms = time_ms(s, e0, e1, [&] {
                         launch_smoother<float>(*h, s, dd.as<Lv<float>>(), di.as<Item>(), nitems,
                                                0.8, h->nz, 0, true, Ls.n % 32 == 0, l);
@@ -1840,6 +1849,7 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
                 sh.ctas = keep.ctas;
                 sh.ring = keep.ring;
                 sh.tmem = keep.tmem;
+                sh.staged = keep.staged;
                 if (l == 0) ms0 = best;
             }
             // (b) the transfers of small levels: how far to split them along
@@ -1939,18 +1949,21 @@ ellsolve_status ellsolve_get_tuning(ellsolve_t h, int *ctas_per_sm, int *ring) {
 }
 
 ellsolve_status ellsolve_set_level_tuning(ellsolve_t h, int level, int ctas_per_sm, int ring,
-                                          int tmem, int restrict_chunk, int prolong_chunk) {
+                                          int tmem, int staged, int restrict_chunk,
+                                          int prolong_chunk) {
     ELLS_GUARD_BEGIN
     if (!h || level < 0 || level >= h->nlev) throw Error(ELLSOLVE_ERR_ARG, "bad handle or level");
     if (ctas_per_sm < 0 || ctas_per_sm > 16) throw Error(ELLSOLVE_ERR_ARG, "ctas_per_sm must be 0..16");
     if (ring != 4 && ring != 8) throw Error(ELLSOLVE_ERR_ARG, "ring must be 4 or 8");
     if (tmem < 0 || tmem > 2) throw Error(ELLSOLVE_ERR_ARG, "tmem must be 0, 1 or 2");
+    if (staged < 0 || staged > 2) throw Error(ELLSOLVE_ERR_ARG, "staged must be 0, 1 or 2");
     if (restrict_chunk < 1 || prolong_chunk < 1)
         throw Error(ELLSOLVE_ERR_ARG, "chunk targets must be >= 1");
     LevelShape &sh = h->shape[size_t(level)];
     sh.ctas = ctas_per_sm;
     sh.ring = ring;
     sh.tmem = tmem;
+    sh.staged = staged;
     sh.restrict_chunk = restrict_chunk;
     sh.prolong_chunk = prolong_chunk;
     if (h->plan) h->plan->drop_graph();
@@ -1959,13 +1972,15 @@ ellsolve_status ellsolve_set_level_tuning(ellsolve_t h, int level, int ctas_per_
 }
 
 ellsolve_status ellsolve_get_level_tuning(ellsolve_t h, int level, int *ctas_per_sm, int *ring,
-                                          int *tmem, int *restrict_chunk, int *prolong_chunk) {
+                                          int *tmem, int *staged, int *restrict_chunk,
+                                          int *prolong_chunk) {
     ELLS_GUARD_BEGIN
     if (!h || level < 0 || level >= h->nlev) throw Error(ELLSOLVE_ERR_ARG, "bad handle or level");
     const LevelShape &sh = h->shape[size_t(level)];
     if (ctas_per_sm) *ctas_per_sm = sh.ctas;
     if (ring) *ring = sh.ring;
     if (tmem) *tmem = sh.tmem;
+    if (staged) *staged = sh.staged;
     if (restrict_chunk) *restrict_chunk = sh.restrict_chunk;
     if (prolong_chunk) *prolong_chunk = sh.prolong_chunk;
     return ELLSOLVE_OK;

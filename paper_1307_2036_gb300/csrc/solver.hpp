@@ -78,6 +78,8 @@ struct LevelShape {
     int ring = 8;   // twisted smoother: staging ring depth, 4 or 8 steps
     int tmem = 0;   // twisted smoother: f' in tensor memory 0 on launches of >= 152
                     // CTAs, 1 always (n_z <= 256), 2 never
+    int staged = 0;  // fully staged smoother: 0 on launches of fewer than 152 blocks
+                     // of 128 columns, 1 always, 2 never (where it fits)
     int restrict_chunk = 608;  // residual + restriction from this level, and the
     int prolong_chunk = 608;   // prolongation onto it: launches of fewer blocks are split
                                // along the vertical until about this many exist

@@ -75,8 +75,8 @@ _SIGS = {
     "ellsolve_set_tuning": (_st, [_vp, _i, _i]),
     "ellsolve_selftest": (_st, [C.c_uint64, C.POINTER(C.c_uint64)]),
     "ellsolve_get_tuning": (_st, [_vp, C.POINTER(_i), C.POINTER(_i)]),
-    "ellsolve_set_level_tuning": (_st, [_vp, _i, _i, _i, _i, _i, _i]),
-    "ellsolve_get_level_tuning": (_st, [_vp, _i] + [C.POINTER(_i)] * 5),
+    "ellsolve_set_level_tuning": (_st, [_vp, _i, _i, _i, _i, _i, _i, _i]),
+    "ellsolve_get_level_tuning": (_st, [_vp, _i] + [C.POINTER(_i)] * 6),
     "ellsolve_server_create": (_st, [C.c_size_t, _i, _vp, C.POINTER(_vp)]),
     "ellsolve_submit": (_st, [_vp, C.POINTER(ellsolve_grid), _d, _d, C.POINTER(C.c_double), _vp,
                               _vp, _d, _i, C.POINTER(C.c_uint64)]),
@@ -224,15 +224,16 @@ class Solver:
         check(_lib.ellsolve_get_tuning(self.h, C.byref(c), C.byref(r)), "get_tuning")
         return c.value, r.value
 
-    def set_level_tuning(self, level, ctas_per_sm, ring, tmem=0, restrict_chunk=608,
+    def set_level_tuning(self, level, ctas_per_sm, ring, tmem=0, staged=0, restrict_chunk=608,
                          prolong_chunk=608):
         check(_lib.ellsolve_set_level_tuning(self.h, int(level), int(ctas_per_sm), int(ring),
-                                             int(tmem), int(restrict_chunk), int(prolong_chunk)),
+                                             int(tmem), int(staged), int(restrict_chunk),
+                                             int(prolong_chunk)),
               "set_level_tuning")
 
     def level_tuning(self, level):
-        """(ctas per SM, ring, tmem, restrict chunk, prolong chunk) of one level."""
-        v = [C.c_int() for _ in range(5)]
+        """(ctas per SM, ring, tmem, staged, restrict chunk, prolong chunk) of one level."""
+        v = [C.c_int() for _ in range(6)]
         check(_lib.ellsolve_get_level_tuning(self.h, int(level), *[C.byref(x) for x in v]),
               "get_level_tuning")
         return tuple(x.value for x in v)

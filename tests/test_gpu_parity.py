@@ -314,17 +314,19 @@ def test_autotune_changes_no_result(torch_mod, oracle_mod):
     ctas, ms = sv.autotune()
     assert 2 <= ctas <= 6 and ms > 0
     for level in range(sv.nlevels):
-        c, ring, tmem, rc, pc = sv.level_tuning(level)
-        print(f"level {level}: ctas {c} ring {ring} tmem {tmem} restrict chunk {rc} prolong chunk {pc}")
-        assert 0 <= c <= 16 and ring in (4, 8) and tmem in (0, 1, 2) and rc >= 1 and pc >= 1
+        c, ring, tmem, stg, rc, pc = sv.level_tuning(level)
+        print(f"level {level}: ctas {c} ring {ring} tmem {tmem} staged {stg} restrict chunk {rc} "
+              f"prolong chunk {pc}")
+        assert 0 <= c <= 16 and ring in (4, 8) and tmem in (0, 1, 2) and stg in (0, 1, 2)
+        assert rc >= 1 and pc >= 1
     sv.solve(f, x2, rtol=1e-9, maxit=40)
     torch.cuda.synchronize()
     assert torch.equal(x1, x2)
 
 
-SHAPES = [  # (ctas per SM, ring, tmem, restrict chunk, prolong chunk) on every level
-    (3, 8, 0, 608, 608), (5, 4, 2, 152, 152), (4, 8, 1, 1216, 1216), (4, 4, 1, 304, 304),
-    (0, 8, 2, 1, 1),
+SHAPES = [  # (ctas per SM, ring, tmem, staged, restrict chunk, prolong chunk) on every level
+    (3, 8, 0, 0, 608, 608), (5, 4, 2, 2, 152, 152), (4, 8, 1, 2, 1216, 1216),
+    (4, 4, 1, 1, 304, 304), (0, 8, 2, 1, 1, 1), (4, 8, 0, 2, 608, 608),
 ]
 
 
@@ -332,7 +334,8 @@ SHAPES = [  # (ctas per SM, ring, tmem, restrict chunk, prolong chunk) on every 
 def test_every_launch_shape_gives_the_same_bits(torch_mod, oracle_mod, kind, n, nz):
     """Each candidate the autotuner may choose, set on every level, gives a
     solve bit-identical to the default shapes (levels with >= 152 blocks of 128
-    columns, the tensor-memory switch forced both ways, n % 32 == 0 and not)."""
+    columns, the tensor-memory switch forced both ways, the fully staged
+    smoother forced both ways, n % 32 == 0 and not)."""
     from paper_1307_2036_gb300 import ellsolve
     torch = torch_mod
     sv = ellsolve.Solver(kind, n, nz, inputs.radial_levels(nz, graded=True), 0.02, 2.0,
