@@ -258,8 +258,19 @@ def run_ours(args, rank, world, local_rank):
         x_host = torch.empty_like(f_host).pin_memory()
     stream.synchronize()
     N = sv.N
-    tuned_ctas, tuned_ms = sv.autotune()
+    if args.shapes_in:
+        # the launch shapes an earlier run's autotuner chose (for a profiled
+        # rerun of the same launches: timing under a profiler is distorted)
+        with open(args.shapes_in) as fh:
+            for l, shp in enumerate(json.load(fh)):
+                sv.set_level_tuning(l, *shp)
+        tuned_ctas = sv.level_tuning(0)[0]
+    else:
+        tuned_ctas, tuned_ms = sv.autotune()
     level_shapes = [list(sv.level_tuning(l)) for l in range(sv.nlevels)]
+    if args.shapes_out:
+        with open(args.shapes_out, "w") as fh:
+            json.dump(level_shapes, fh)
 
     def solve():
         st, res = sv.solve(f, x, rtol=rtol, maxit=60)
@@ -479,11 +490,11 @@ def run_accuracy(torch, stream, workload):
 
 
 def run_configs(torch, stream):
-    """The small configurations beside the benchmark workload.  C1: box 32x32,
+    """The small workloads beside the benchmark workload.  box32: box 32x32,
     n_z = 32 uniform on [1, 1.01], omega^2 = 0.01, lambda = 1, seeded uniform
     and manufactured (3, 5) x cos m = 2 right-hand sides, time to 1e-5 for FP64
     multigrid, mixed precision and PCG (latency-bound: time to solution, not a
-    roofline).  C2: box 256x256, n_z = 64 graded, the 9 cases omega^2 x lambda
+    roofline).  box256_sweep: box 256x256, n_z = 64 graded, the 9 cases omega^2 x lambda
     with a uniform right-hand side: FP64 multigrid and PCG to 1e-5, mixed
     precision to 1e-10 (V-cycles or iterations, time, status)."""
     import numpy as np
@@ -504,7 +515,7 @@ def run_configs(torch, stream):
     solvers = (("fp64 multigrid", dict(precision=0), 1e-5, 100),
                ("mixed multigrid", dict(precision=1, use_graph=1), 1e-5, 100),
                ("fp64 pcg", dict(precision=0, solver=1), 1e-5, 2000))
-    out = {"C1": {"workload": "box 32x32x32 uniform, omega2 0.01, lambda 1, rtol 1e-5"}}
+    out = {"box32": {"workload": "box 32x32x32 uniform, omega2 0.01, lambda 1, rtol 1e-5"}}
     r1 = inputs.radial_levels(32)
     for rhs_name, fh in (("uniform", inputs.uniform_pm1((32, 1, 32, 32))),
                          ("manufactured", inputs.fourier_cos_mode(32, 32))):
@@ -514,7 +525,7 @@ def run_configs(torch, stream):
         stream.synchronize()
         for name, kw, rtol, maxit in solvers:
             sv = ellsolve.Solver(0, 32, 32, r1, 0.01, 1.0, stream=stream.cuda_stream, **kw)
-            out["C1"][f"{rhs_name}, {name}"] = timed(sv, f, x, rtol, maxit)
+            out["box32"][f"{rhs_name}, {name}"] = timed(sv, f, x, rtol, maxit)
             sv.close()
     nb, nzb = 256, 64
     rb = inputs.radial_levels(nzb, graded=True)
@@ -522,7 +533,7 @@ def run_configs(torch, stream):
         fb = torch.from_numpy(rhs_for(0, nb, nzb, "uniform")).to("cuda")
         xb = torch.zeros_like(fb)
     stream.synchronize()
-    out["C2"] = {"workload": "box 256x256x64 graded, uniform RHS; multigrid and PCG to 1e-5, "
+    out["box256_sweep"] = {"workload": "box 256x256x64 graded, uniform RHS; multigrid and PCG to 1e-5, "
                              "mixed precision to 1e-10", "cases": []}
     for w2 in (1e-3, 1e-2, 1e-1):
         for lam in (0.1, 1.0, 10.0):
@@ -534,7 +545,7 @@ def run_configs(torch, stream):
                                      **kw)
                 case[name] = timed(sv, fb, xb, rtol, maxit)
                 sv.close()
-            out["C2"]["cases"].append(case)
+            out["box256_sweep"]["cases"].append(case)
     del fb, xb
     torch.cuda.empty_cache()
     return out
@@ -598,7 +609,7 @@ def run_smoothers(torch, stream, workload, reps=3):
 
 
 def run_ensemble(torch, stream, members=32, n=128, nz=64, rtol=1e-8, reps=3):
-    """Config 4: `members` independent cubed-sphere problems 6 x n^2 x nz with
+    """Ensemble: `members` independent cubed-sphere problems 6 x n^2 x nz with
     per-member omega^2 (log-uniform [1e-3, 1e-1]) and lambda (uniform [0.5, 5]),
     uniform right-hand sides; one batched mixed-precision solve (one launch per
     kernel and level over all members) against the same solves done one after
@@ -719,12 +730,12 @@ def _fifo(arrival, service):
 
 def run_serving(torch, stream, count, rate=200.0, low_count=1000, low_rate=60.0,
                 budget=64 << 30, slots=16):
-    """Config 5 through the continuous-batching server: Poisson arrivals, n in
-    {48, 96, 192, 384}, nz in {32, 64, 128}, tol in {1e-5, 1e-10}, omega^2 and
-    lambda as in config 4.  Two runs: `count` requests offered at `rate` per
-    second (config 5's rate, above the server's capacity, so the queue grows;
-    `count` is bounded by the device memory the outstanding requests'
-    solution buffers need), and `low_count` requests at `low_rate`, below
+    """Mixed-size requests through the continuous-batching server: Poisson
+    arrivals at 200/s, n in {48, 96, 192, 384}, nz in {32, 64, 128}, tol in
+    {1e-5, 1e-10}, omega^2 and lambda drawn as in the ensemble.  Two runs:
+    `count` requests offered at `rate` per second (above the server's
+    capacity, so the queue grows; `count` is bounded by the device memory
+    the outstanding requests' solution buffers need), and `low_count` requests at `low_rate`, below
     capacity.  Baseline: plain FP64 multigrid one request at a time in FIFO
     order over the same arrivals, with the service time of each (n, nz, tol)
     class measured once on the GPU (the class's first request)."""
@@ -733,7 +744,7 @@ def run_serving(torch, stream, count, rate=200.0, low_count=1000, low_rate=60.0,
     from paper_1307_2036_gb300 import ellsolve, inputs
     runs = {}
     fifo_cache = {}
-    for name, cnt, rt, seed_off in (("offered_at_config_rate", count, rate, 0),
+    for name, cnt, rt, seed_off in (("offered_at_200_per_s", count, rate, 0),
                                     ("below_capacity", low_count, low_rate, 1)):
         req = inputs.request_stream(cnt, rate=rt, seed=inputs.DEFAULT_SEED + seed_off)
         shapes = {}
@@ -783,9 +794,9 @@ def run_serving(torch, stream, count, rate=200.0, low_count=1000, low_rate=60.0,
                                    "p99_latency_s": float(np.percentile(base, 99))}}
         del shapes
         torch.cuda.empty_cache()
-    return {"workload": "config 5 requests: n in 48..384, nz in 32..128, tol 1e-5/1e-10; "
+    return {"workload": "mixed-size requests: n in 48..384, nz in 32..128, tol 1e-5/1e-10; "
                         f"server {slots} slots, {budget >> 30} GiB budget",
-            "sample": (f"{count} of config 5's 10,000 requests at {rate:g}/s (the queue grows "
+            "sample": (f"{count} of a 10,000-request stream at {rate:g}/s (the queue grows "
                        "above capacity and every outstanding request holds its solution "
                        "buffer on the device, which bounds the sample), and "
                        f"{low_count} requests at {low_rate:g}/s below capacity"),
@@ -796,7 +807,7 @@ def run_serving(torch, stream, count, rate=200.0, low_count=1000, low_rate=60.0,
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
-KERNEL_REV = "smooth-v9-twisted-tmem"
+KERNEL_REV = "smooth-v10-twisted-pairs"
 
 
 def main():
@@ -810,8 +821,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ensemble and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=1500,
-                    help="requests of the serving run at config 5's rate (bounded by the device "
+                    help="requests of the serving run at 200/s (bounded by the device "
                          "memory that outstanding solution buffers need)")
+    ap.add_argument("--shapes-out", default=None,
+                    help="write the autotuned per-level launch shapes to this JSON file")
+    ap.add_argument("--shapes-in", default=None,
+                    help="take the per-level launch shapes from this JSON file instead of "
+                         "autotuning")
     ap.add_argument("--inner-cycles", type=int, default=3,
                     help="FP32 V-cycles per FP64 refinement step")
     args = ap.parse_args()
