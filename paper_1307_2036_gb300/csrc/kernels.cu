@@ -825,18 +825,21 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
 // ---------------------------------------------------------------------------
 // Line smoother for small launches (fewer blocks than SMs), fully staged.  The
 // same twisted elimination and arithmetic as k_smooth_tw, one column per
-// thread with the two halves as the lanes of FP32x2 arithmetic, but a CTA is
-// one warp (32 columns) and copies every level it needs -- the own rows with a
-// halo column each side, b, rows j-1 and j+1 (34 aligned 16-byte chunks per
-// level), and the neighbours off the staged rows into separate arrays -- into
-// shared memory before it starts.  The elimination and the back substitution
-// then run with no barrier or copy wait inside their loops, so the loads of
-// later steps are issued early; f' and c' of every step are parked in tensor
-// memory (2 columns per step each).  A small launch is bound by the latency of
-// the column's sequential sweep, which this shortens; a large one by memory,
-// where the streaming ring of k_smooth_tw is the right design.
+// thread with the two halves as the lanes of FP32x2 arithmetic, but a CTA
+// takes 32 columns.  Its four warps copy every level those columns need -- the
+// own rows with a halo column each side, b, rows j-1 and j+1 (34 aligned
+// 16-byte chunks per level), and the neighbours off the staged rows into
+// separate arrays -- into shared memory, then form the residual of every level
+// (a quarter of the steps each; it has no sequential dependence) over b.  Warp
+// 0 alone then runs the elimination and the back substitution, with no barrier
+// or copy wait inside their loops and only the recurrences on its path; f' and
+// c' of every step are parked in tensor memory (2 columns per step each).  A
+// small launch is bound by the latency of the column's sequential sweep, which
+// this shortens; a large one by memory, where the streaming ring of
+// k_smooth_tw is the right design.
 // ---------------------------------------------------------------------------
 constexpr int kStgF = 136;  // floats per staged level: [own 40][b 32][j-1 32][j+1 32]
+constexpr int kStgW = 4;    // warps of a staged CTA: all copy and form residuals, warp 0 eliminates
 
 __host__ __device__ inline size_t stg_smem_bytes(int max_nz) {
     return size_t(max_nz) * kStgF * 4 +   // staged rows
@@ -848,9 +851,9 @@ __host__ __device__ inline size_t stg_smem_bytes(int max_nz) {
 __host__ __device__ inline int stg_tmem_half(int max_nz) { return tw_tmem_cols(max_nz); }
 
 template <int ZERO>
-__global__ void __launch_bounds__(32) k_smooth_stg(const Lv<float> *__restrict__ L,
-                                                   const Item *__restrict__ items, float rho,
-                                                   int max_nz) {
+__global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__restrict__ L,
+                                                           const Item *__restrict__ items,
+                                                           float rho, int max_nz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *stg = reinterpret_cast<float *>(smem_raw);
     float *hb = stg + size_t(max_nz) * kStgF;  // [level][lane]
@@ -861,14 +864,14 @@ __global__ void __launch_bounds__(32) k_smooth_stg(const Lv<float> *__restrict__
     const Item it = items[blockIdx.x >> 2];
     const Lv<float> &d = L[it.lv];
     const int nc = d.ncol, nz = d.nz, n = d.n, m = nz / 2;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0w = it.col0 + 32 * int(blockIdx.x & 3);
-    const int c = c0w + lane;
+    const int c = c0w + lane;  // every warp's lane l stands for the same column
     const bool active = c < nc;
     const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
     constexpr bool zero = ZERO == 1;
     const unsigned half = unsigned(stg_tmem_half(max_nz));
-    tm_alloc(tm_sh, 2u * half);
+    if (warp == 0) tm_alloc(tm_sh, 2u * half);
     const float *__restrict__ u = d.u[it.in];
     float *__restrict__ un = d.u[it.out];
     const float *__restrict__ b = d.b;
@@ -893,8 +896,9 @@ __global__ void __launch_bounds__(32) k_smooth_stg(const Lv<float> *__restrict__
             if (nbr.w != c + n) { vd = 3; vc = nbr.w; }
         }
     }
-    // staging: lane l copies chunk l (and lanes 0, 1 chunks 32, 33) of every
-    // level; chunk r: 0..9 own row c0w-4.., 10..17 b, 18..25 row j-1, 26..33 row j+1
+    // staging: lane l copies chunk l (and lanes 0, 1 chunks 32, 33) of the
+    // levels k = w, w + 4, ... of its warp w; chunk r: 0..9 own row c0w-4..,
+    // 10..17 b, 18..25 row j-1, 26..33 row j+1
     for (int r = lane; r < 34; r += 32) {
         const float *base;
         int scol, dst;
@@ -904,35 +908,37 @@ __global__ void __launch_bounds__(32) k_smooth_stg(const Lv<float> *__restrict__
         else if (r < 26) { base = u; scol = c0w - n + 4 * (r - 18); dst = kJmT + 4 * (r - 18); use = !zero; }
         else { base = u; scol = c0w + n + 4 * (r - 26); dst = kJpT + 4 * (r - 26); use = !zero; }
         if (use && scol >= 0 && scol + 4 <= nc)
-            for (int k = 0; k < nz; ++k) cp_async16(stg + k * kStgF + dst, base + k * snc + scol, 16);
+            for (int k = warp; k < nz; k += kStgW)
+                cp_async16(stg + k * kStgF + dst, base + k * snc + scol, 16);
     }
     if (hd >= 0)
-        for (int k = 0; k < nz; ++k) cp_async(hb + k * 32 + lane, u + k * snc + hc, true);
+        for (int k = warp; k < nz; k += kStgW) cp_async(hb + k * 32 + lane, u + k * snc + hc, true);
     if (vd >= 0)
-        for (int k = 0; k < nz; ++k) cp_async(vb + k * 32 + lane, u + k * snc + vc, true);
+        for (int k = warp; k < nz; k += kStgW) cp_async(vb + k * 32 + lane, u + k * snc + vc, true);
     cp_async_commit();
-    for (int i = lane; i < m; i += 32) {
+    for (int i = tid; i < m; i += 32 * kStgW) {
         VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
         GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
     }
     cp_async_wait<0>();
     tm_fence_before();
-    __syncwarp();
+    __syncthreads();
     tm_fence_after();
-    const unsigned tm = *tm_sh;
     const int own = kOwnT + 4 + lane;
 
-    float2 u0 = f2(0.f), um = f2(0.f);
-    if (!zero) u0 = make_float2(stg[own], stg[(nz - 1) * kStgF + own]);
-    float2 ratio = f2(0.f), fp = f2(0.f), lo = f2(0.f), lo_g = f2(0.f);
-    Piv2 pv;
-    pv.cp = pv.inv = pv.ratio_next = f2(0.f);
-#pragma unroll 4
-    for (int s = 0; s < m; ++s) {
-        const float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
-        float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
-        const float2 hi_g = GH[s], Vp = VP[s];
-        if (!zero) {
+    // The residual r = b - A u of every step (levels s and nz-1-s) has no
+    // sequential dependence: warp w forms it for steps [w m/4, (w+1) m/4), with
+    // the operations and operand values of the sequential sweep, and writes it
+    // over b.  Warp 0 then runs the elimination alone.
+    if (!zero) {
+        const int q = m / kStgW;
+        for (int s = warp * q; s < (warp + 1) * q; ++s) {
+            float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
+            float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
+            const float2 hi_g = GH[s], Vp = VP[s];
+            const float2 lo_g = s == 0 ? f2(0.f) : GH[s - 1];
+            const float2 u0 = make_float2(lk[own], lt[own]);
+            const float2 um = s == 0 ? f2(0.f) : make_float2(lk[own - kStgF], lt[own + kStgF]);
             // the next level of each half; at the meeting step the other half's
             const float2 up = s == m - 1 ? make_float2(lt[own], lk[own])
                                          : make_float2(lk[kStgF + own], lt[own - kStgF]);
@@ -958,17 +964,28 @@ __global__ void __launch_bounds__(32) k_smooth_stg(const Lv<float> *__restrict__
             Au = __ffma2_rn(Vp, horiz, Au);
             Au = __ffma2_rn(f2(A), vert, Au);
             r = sub2(r, Au);
-            um = u0;
-            u0 = up;
+            lk[kBT + lane] = r.x;
+            lt[kBT + lane] = r.y;
         }
-        const float2 hi = __fmul2_rn(f2(A), hi_g);
-        pv = pivot2(__fmul2_rn(Vp, f2(sv)), lo, hi, ratio);
+        __syncthreads();
+    }
+    if (warp != 0) return;
+    const unsigned tm = *tm_sh;
+
+    float2 ratio = f2(0.f), fp = f2(0.f), lo = f2(0.f);
+    Piv2 pv;
+    pv.cp = pv.inv = pv.ratio_next = f2(0.f);
+#pragma unroll 4
+    for (int s = 0; s < m; ++s) {
+        const float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
+        const float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
+        const float2 hi = __fmul2_rn(f2(A), GH[s]);
+        pv = pivot2(__fmul2_rn(VP[s], f2(sv)), lo, hi, ratio);
         fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
         tm_st2(tm + 2u * unsigned(s), fp);
         tm_st2(tm + half + 2u * unsigned(s), pv.cp);
         ratio = pv.ratio_next;
         lo = hi;
-        lo_g = hi_g;
     }
     // meeting of the halves: x_{m-1} and x_m from the two last equations
     float2 x;
@@ -2120,7 +2137,7 @@ static cudaError_t launch_stg_z(cudaStream_t s, const Lv<float> *L, const Item *
     if (cap > bytes) bytes = cap;
     cudaError_t e = set_smem(k_smooth_stg<Z>, bytes);
     if (e != cudaSuccess) return e;
-    k_smooth_stg<Z><<<unsigned(nitems) * 4u, 32, bytes, s>>>(L, items, rho, max_nz);
+    k_smooth_stg<Z><<<unsigned(nitems) * 4u, 32 * kStgW, bytes, s>>>(L, items, rho, max_nz);
     return cudaGetLastError();
 }
 
