@@ -826,20 +826,20 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
 // Line smoother for small launches (fewer blocks than SMs), fully staged.  The
 // same twisted elimination and arithmetic as k_smooth_tw, one column per
 // thread with the two halves as the lanes of FP32x2 arithmetic, but a CTA
-// takes 32 columns.  Its four warps copy every level those columns need -- the
+// takes 32 columns.  Its eight warps copy every level those columns need -- the
 // own rows with a halo column each side, b, rows j-1 and j+1 (34 aligned
 // 16-byte chunks per level), and the neighbours off the staged rows into
-// separate arrays -- into shared memory, then form the residual of every level
-// (a quarter of the steps each; it has no sequential dependence) over b.  Warp
-// 0 alone then runs the elimination and the back substitution, with no barrier
-// or copy wait inside their loops and only the recurrences on its path; f' and
-// c' of every step are parked in tensor memory (2 columns per step each).  A
-// small launch is bound by the latency of the column's sequential sweep, which
-// this shortens; a large one by memory, where the streaming ring of
-// k_smooth_tw is the right design.
+// separate arrays -- into shared memory.  Then warp 0 runs the pivot
+// recurrence while the other warps form the residual of every level over b
+// (neither depends on the elimination), and warp 0 alone runs the f'
+// recurrence and the back substitution, with no barrier or copy wait inside
+// their loops; the inverse pivots and f' of every step are parked in tensor
+// memory (2 columns per step each).  A small launch is bound by the latency of
+// the column's sequential sweep, which this shortens; a large one by memory,
+// where the streaming ring of k_smooth_tw is the right design.
 // ---------------------------------------------------------------------------
 constexpr int kStgF = 136;  // floats per staged level: [own 40][b 32][j-1 32][j+1 32]
-constexpr int kStgW = 4;    // warps of a staged CTA: all copy and form residuals, warp 0 eliminates
+constexpr int kStgW = 8;    // warps of a staged CTA: all copy; warp 0 eliminates, the rest form residuals
 
 __host__ __device__ inline size_t stg_smem_bytes(int max_nz) {
     return size_t(max_nz) * kStgF * 4 +   // staged rows
@@ -897,7 +897,7 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
         }
     }
     // staging: lane l copies chunk l (and lanes 0, 1 chunks 32, 33) of the
-    // levels k = w, w + 4, ... of its warp w; chunk r: 0..9 own row c0w-4..,
+    // levels k = w, w + 8, ... of its warp w; chunk r: 0..9 own row c0w-4..,
     // 10..17 b, 18..25 row j-1, 26..33 row j+1
     for (int r = lane; r < 34; r += 32) {
         const float *base;
@@ -926,13 +926,29 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
     tm_fence_after();
     const int own = kOwnT + 4 + lane;
 
-    // The residual r = b - A u of every step (levels s and nz-1-s) has no
-    // sequential dependence: warp w forms it for steps [w m/4, (w+1) m/4), with
-    // the operations and operand values of the sequential sweep, and writes it
-    // over b.  Warp 0 then runs the elimination alone.
-    if (!zero) {
-        const int q = m / kStgW;
-        for (int s = warp * q; s < (warp + 1) * q; ++s) {
+    // Neither the pivots (they depend on the coefficients only) nor the
+    // residual r = b - A u of a step (levels s and nz-1-s) depend on the
+    // elimination.  Warp 0 runs the pivot recurrence and parks 1/pivot of
+    // every step in tensor memory while warps 1..7 form the residuals (every
+    // seventh step each, with the operations and operand values of the
+    // sequential sweep) over b.  Warp 0 then runs the f' recurrence and the
+    // back substitution alone, with c' = hi / pivot recomputed from the parked
+    // value (the same product, so the same bits).
+    const unsigned tm = *tm_sh;  // inverse pivots in columns [0, half), f' in [half, 2 half)
+    Piv2 pv;
+    pv.cp = pv.inv = pv.ratio_next = f2(0.f);
+    if (warp == 0) {
+        float2 ratio = f2(0.f), lo = f2(0.f);
+#pragma unroll 4
+        for (int s = 0; s < m; ++s) {
+            const float2 hi = __fmul2_rn(f2(A), GH[s]);
+            pv = pivot2(__fmul2_rn(VP[s], f2(sv)), lo, hi, ratio);
+            tm_st2(tm + 2u * unsigned(s), pv.inv);
+            ratio = pv.ratio_next;
+            lo = hi;
+        }
+    } else if (!zero) {
+        for (int s = warp - 1; s < m; s += kStgW - 1) {
             float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
             float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
             const float2 hi_g = GH[s], Vp = VP[s];
@@ -967,25 +983,27 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
             lk[kBT + lane] = r.x;
             lt[kBT + lane] = r.y;
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (warp != 0) return;
-    const unsigned tm = *tm_sh;
+    tm_wait_st();
 
-    float2 ratio = f2(0.f), fp = f2(0.f), lo = f2(0.f);
-    Piv2 pv;
-    pv.cp = pv.inv = pv.ratio_next = f2(0.f);
-#pragma unroll 4
-    for (int s = 0; s < m; ++s) {
-        const float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
-        const float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
-        const float2 hi = __fmul2_rn(f2(A), GH[s]);
-        pv = pivot2(__fmul2_rn(VP[s], f2(sv)), lo, hi, ratio);
-        fp = __fmul2_rn(__ffma2_rn(lo, fp, r), pv.inv);
-        tm_st2(tm + 2u * unsigned(s), fp);
-        tm_st2(tm + half + 2u * unsigned(s), pv.cp);
-        ratio = pv.ratio_next;
-        lo = hi;
+    // f' of every step, eight steps per tensor-memory load of the inverse pivots
+    float2 fp = f2(0.f), lo = f2(0.f);
+    for (int kb = 0; kb < m / 8; ++kb) {
+        unsigned iv[16];
+        tm_ld<8>(tm + 2u * unsigned(kb * 8), iv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int s = kb * 8 + j;
+            const float *lk = stg + s * kStgF, *lt = stg + (nz - 1 - s) * kStgF;
+            const float2 r = make_float2(lk[kBT + lane], lt[kBT + lane]);
+            const float2 hi = __fmul2_rn(f2(A), GH[s]);
+            const float2 inv = make_float2(__uint_as_float(iv[2 * j]), __uint_as_float(iv[2 * j + 1]));
+            fp = __fmul2_rn(__ffma2_rn(lo, fp, r), inv);
+            tm_st2(tm + half + 2u * unsigned(s), fp);
+            lo = hi;
+        }
     }
     // meeting of the halves: x_{m-1} and x_m from the two last equations
     float2 x;
@@ -997,14 +1015,15 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
     tm_wait_st();
     // back substitution, step s = m-1 .. 0, eight steps per tensor-memory load
     for (int kb = m / 8 - 1; kb >= 0; --kb) {
-        unsigned fv[16], cv[16];
-        tm_ld<8>(tm + 2u * unsigned(kb * 8), fv);
-        tm_ld<8>(tm + half + 2u * unsigned(kb * 8), cv);
+        unsigned fv[16], iv[16];
+        tm_ld<8>(tm + half + 2u * unsigned(kb * 8), fv);
+        tm_ld<8>(tm + 2u * unsigned(kb * 8), iv);
 #pragma unroll
         for (int jj = 7; jj >= 0; --jj) {
             const int s = kb * 8 + jj;
             const float2 fk = make_float2(__uint_as_float(fv[2 * jj]), __uint_as_float(fv[2 * jj + 1]));
-            const float2 ck = make_float2(__uint_as_float(cv[2 * jj]), __uint_as_float(cv[2 * jj + 1]));
+            const float2 inv = make_float2(__uint_as_float(iv[2 * jj]), __uint_as_float(iv[2 * jj + 1]));
+            const float2 ck = __fmul2_rn(__fmul2_rn(f2(A), GH[s]), inv);
             const float2 uo = zero ? f2(0.f)
                                    : make_float2(stg[s * kStgF + own], stg[(nz - 1 - s) * kStgF + own]);
             if (s != m - 1) x = __ffma2_rn(ck, x, fk);
