@@ -1666,6 +1666,72 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
 // keeps the bound and recomputes the residual in FP64 when the tracked value
 // is no longer accurate to 0.1%.
 // ---------------------------------------------------------------------------
+// The per-column constants and the per-level arithmetic of a tracked step
+// (one column, level k): e0 = e_k, ep = e_{k+1} (0 above the top), the four
+// horizontal neighbours' e_k, (V_k, g_{k+1}) as double-float, the stored
+// scaled residual rv and x_k.  Returns the new stored residual (nh, nl), and
+// x_k + e_k / s; accumulates the column sums.
+struct TrackCol {
+    ff A, S, T0, T1, T2, T3;
+    int kx;       // s = 2^-kx
+    float ratio;  // s_next / s, a power of two
+};
+struct TrackOut {
+    float nh, nl;
+    double x;
+};
+__device__ __forceinline__ TrackCol track_col(const Column<double> &col, double sc, double sn) {
+    TrackCol tc;
+    const long long sb = __double_as_longlong(sc);
+    tc.kx = 1023 - static_cast<int>((sb >> 52) & 0x7ff);  // sc = 2^-kx
+    tc.ratio = float(sn / sc);                           // a power of two
+    tc.A = split_ff(col.A);
+    tc.S = split_ff(col.s);
+    tc.T0 = split_ff(col.t0);
+    tc.T1 = split_ff(col.t1);
+    tc.T2 = split_ff(col.t2);
+    tc.T3 = split_ff(col.t3);
+    return tc;
+}
+__device__ __forceinline__ TrackOut track_level(const TrackCol &tc, float e0, float ep, float ew,
+                                                float ee, float es, float en, float2 v2,
+                                                float2 g2, float2 rv, double xv, ff &flux_lo,
+                                                float &colsum, float &magsum, float &esum) {
+    // s e - sum_q t_q e_q: the hi parts summed by TwoSum, every error and lo
+    // part collected in one float
+    const ff p0 = mul_ff_f(tc.S, e0);
+    const ff p1 = mul_ff_f(neg_ff(tc.T0), ew);
+    const ff p2 = mul_ff_f(neg_ff(tc.T1), ee);
+    const ff p3 = mul_ff_f(neg_ff(tc.T2), es);
+    const ff p4 = mul_ff_f(neg_ff(tc.T3), en);
+    ff t = two_sum(p0.hi, p1.hi);
+    float err = __fadd_rn(__fadd_rn(p0.lo, p1.lo), t.lo);
+    t = two_sum(t.hi, p2.hi);
+    err = __fadd_rn(err, __fadd_rn(p2.lo, t.lo));
+    t = two_sum(t.hi, p3.hi);
+    err = __fadd_rn(err, __fadd_rn(p3.lo, t.lo));
+    t = two_sum(t.hi, p4.hi);
+    err = __fadd_rn(err, __fadd_rn(p4.lo, t.lo));
+    const ff hm = two_sum(t.hi, err);
+    const ff Vk = {v2.x, v2.y}, gk1 = {g2.x, g2.y};
+    // vertical: face flux g_{k+1} (e_k - e_{k+1}), carried to the next level
+    const ff flux_hi = mul_ff(gk1, two_sum(e0, -ep));
+    const ff Ae = add_ff(mul_ff(Vk, hm), mul_ff(tc.A, add_ff(flux_hi, neg_ff(flux_lo))));
+    const ff rn = add_ff({rv.x, rv.y}, neg_ff(Ae));
+    TrackOut o;
+    o.nh = __fmul_rn(rn.hi, tc.ratio);
+    o.nl = __fmul_rn(rn.lo, tc.ratio);
+    colsum = __fmaf_rn(rn.hi, rn.hi, colsum);
+    const float mag = __fmaf_rn(
+        v2.x, (fabsf(p0.hi) + fabsf(p1.hi)) + (fabsf(p2.hi) + (fabsf(p3.hi) + fabsf(p4.hi))),
+        tc.A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
+    magsum = __fmaf_rn(mag, mag, magsum);
+    o.x = xv + f32_to_f64_pow2(e0, tc.kx);
+    esum = __fmaf_rn(e0, e0, esum);
+    flux_lo = flux_hi;
+    return o;
+}
+
 __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict__ L64,
                                                    const Lv<float> *__restrict__ L32,
                                                    const Item *__restrict__ items,
@@ -1698,13 +1764,8 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
         const Lv<float> &f32 = L32[it.lv];
         const float *__restrict__ e = f32.u[it.in];
         float *__restrict__ r32 = f32.b;
-        const long long sb = __double_as_longlong(sc);
-        const int kx = 1023 - static_cast<int>((sb >> 52) & 0x7ff);  // sc = 2^-kx
-        const float ratio = float(sn / sc);                           // a power of two
         const Column<double> col = load_column(d, c);
-        const ff A = split_ff(col.A), S = split_ff(col.s);
-        const ff T0 = split_ff(col.t0), T1 = split_ff(col.t1), T2 = split_ff(col.t2),
-                 T3 = split_ff(col.t3);
+        const TrackCol tc = track_col(col, sc, sn);
         float colsum = 0.f, magsum = 0.f, esum = 0.f;
         float e0 = __ldg(e + c);
         ff flux_lo = {0.f, 0.f};
@@ -1733,44 +1794,192 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                 if (k >= nz) break;
                 const size_t o = size_t(k) * nc;
                 const float ep = ev[j];
-                // s e - sum_q t_q e_q: the hi parts summed by TwoSum, every
-                // error and lo part collected in one float
-                const ff p0 = mul_ff_f(S, e0);
-                const ff p1 = mul_ff_f(neg_ff(T0), ew[j]);
-                const ff p2 = mul_ff_f(neg_ff(T1), ee[j]);
-                const ff p3 = mul_ff_f(neg_ff(T2), es[j]);
-                const ff p4 = mul_ff_f(neg_ff(T3), en[j]);
-                ff t = two_sum(p0.hi, p1.hi);
-                float err = __fadd_rn(__fadd_rn(p0.lo, p1.lo), t.lo);
-                t = two_sum(t.hi, p2.hi);
-                err = __fadd_rn(err, __fadd_rn(p2.lo, t.lo));
-                t = two_sum(t.hi, p3.hi);
-                err = __fadd_rn(err, __fadd_rn(p3.lo, t.lo));
-                t = two_sum(t.hi, p4.hi);
-                err = __fadd_rn(err, __fadd_rn(p4.lo, t.lo));
-                const ff hm = two_sum(t.hi, err);
-                const float2 v2 = Vh[k], g2 = gh[k + 1];
-                const ff Vk = {v2.x, v2.y}, gk1 = {g2.x, g2.y};
-                // vertical: face flux g_{k+1} (e_k - e_{k+1}), carried to the next level
-                const ff flux_hi = mul_ff(gk1, two_sum(e0, -ep));
-                const ff Ae =
-                    add_ff(mul_ff(Vk, hm), mul_ff(A, add_ff(flux_hi, neg_ff(flux_lo))));
-                const ff rn = add_ff({rv[j].x, rv[j].y}, neg_ff(Ae));
-                const float nh = __fmul_rn(rn.hi, ratio), nl = __fmul_rn(rn.lo, ratio);
-                __stcs(rt + o + c, make_float2(nh, nl));
-                r32[o + c] = nh;
-                colsum = __fmaf_rn(rn.hi, rn.hi, colsum);
-                const float mag = __fmaf_rn(
-                    v2.x,
-                    (fabsf(p0.hi) + fabsf(p1.hi)) + (fabsf(p2.hi) + (fabsf(p3.hi) + fabsf(p4.hi))),
-                    A.hi * (fabsf(flux_hi.hi) + fabsf(flux_lo.hi)));
-                magsum = __fmaf_rn(mag, mag, magsum);
-                __stcs(x + o + c, xv[j] + f32_to_f64_pow2(e0, kx));
-                esum = __fmaf_rn(e0, e0, esum);
-                flux_lo = flux_hi;
+                const TrackOut to = track_level(tc, e0, ep, ew[j], ee[j], es[j], en[j], Vh[k],
+                                                gh[k + 1], rv[j], xv[j], flux_lo, colsum, magsum,
+                                                esum);
+                __stcs(rt + o + c, make_float2(to.nh, to.nl));
+                r32[o + c] = to.nh;
+                __stcs(x + o + c, to.x);
                 e0 = ep;
             }
         }
+        acc = double(colsum);
+        acc2 = double(magsum);
+        acc3 = double(esum);
+    }
+    const double inv2 = 1.0 / (sc * sc);
+    const double t1 = block_sum(acc);
+    __syncthreads();  // block_sum's shared slots are reused
+    const double t2 = block_sum(acc2);
+    __syncthreads();
+    const double t3 = block_sum(acc3);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = t1 * inv2;
+        partials2[blockIdx.x] = t2 * inv2;
+        partials3[blockIdx.x] = t3 * inv2;  // squared norm of the update of x
+    }
+}
+
+// The same step with the streams staged: levels whose n % 32 == 0 (a warp's
+// 32 columns lie in one row of one panel).  Per warp and level, 58 aligned
+// 16-byte cp.async chunks copy e of the own row with a halo column each side
+// (10), e of rows j-1 and j+1 (8 + 8), the stored residual (16) and x (16)
+// into a kTR-level shared-memory ring, so that the loads of kTR - 1 levels are
+// in flight without holding registers; the neighbours off the staged rows
+// (west of lane 0, east of lane 31, the whole row j-1 or j+1 at a panel edge)
+// are copied into the positions of the chunks they replace.  Arithmetic and
+// stores are those of k_ir_track (track_level), so the results are the same
+// bits.
+constexpr int kTR = 8;                       // ring depth (levels)
+constexpr int kTrE = 0, kTrJm = 40, kTrJp = 72, kTrR = 104, kTrX = 168;  // floats in a slot
+constexpr int kTrSlot = 232;                 // floats per warp and slot (58 chunks)
+
+__host__ __device__ inline size_t ir_track_stg_smem(int max_nz) {
+    const size_t vg = (size_t(2 * max_nz + 1) * sizeof(float2) + 15) / 16 * 16;
+    return vg + size_t(kTR) * (kBlk / 32) * kTrSlot * 4;
+}
+
+__global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restrict__ L64,
+                                                       const Lv<float> *__restrict__ L32,
+                                                       const Item *__restrict__ items,
+                                                       const double *__restrict__ scale,
+                                                       const int *__restrict__ sel, int nmembers,
+                                                       int max_nz, double *__restrict__ partials,
+                                                       double *__restrict__ partials2,
+                                                       double *__restrict__ partials3) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *Vh = reinterpret_cast<float2 *>(smem_raw), *gh = Vh + max_nz;
+    float *ring = reinterpret_cast<float *>(smem_raw + (size_t(2 * max_nz + 1) * sizeof(float2) +
+                                                       15) / 16 * 16);
+    const Item it = items[blockIdx.x];
+    if (sel[it.lv] != 1) return;
+    const Lv<double> &d = L64[it.lv];
+    const int nz = d.nz, nc = d.ncol, n = d.n;
+    for (int k = threadIdx.x; k <= nz; k += kBlk) {
+        if (k < nz) {
+            const ff v = split_ff(d.V[k]);
+            Vh[k] = make_float2(v.hi, v.lo);
+        }
+        const ff g = split_ff(d.g[k]);
+        gh[k] = make_float2(g.hi, g.lo);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0w = it.col0 + 32 * warp;
+    const int c = c0w + lane;
+    double acc = 0.0, acc2 = 0.0, acc3 = 0.0;
+    const double sc = scale[it.lv], sn = scale[nmembers + it.lv];
+    if (c0w < nc) {  // ncol % 32 == 0: the warp's columns all exist
+        double *__restrict__ x = d.u[0];
+        float2 *__restrict__ rt = reinterpret_cast<float2 *>(d.aux);
+        const Lv<float> &f32 = L32[it.lv];
+        const float *__restrict__ e = f32.u[it.in];
+        float *__restrict__ r32 = f32.b;
+        const Column<double> col = load_column(d, c);
+        const TrackCol tc = track_col(col, sc, sn);
+        // neighbours off the staged rows: at most one horizontal (hd 0 west,
+        // 1 east) and one vertical (vd 2 south, 3 north)
+        int hd = -1, vd = -1;
+        if (col.nb.x != c - 1) hd = 0;
+        if (col.nb.y != c + 1) hd = 1;
+        if (col.nb.z != c - n) vd = 2;
+        if (col.nb.w != c + n) vd = 3;
+        const int hc = hd == 0 ? col.nb.x : col.nb.y, vc = vd == 2 ? col.nb.z : col.nb.w;
+        const bool skip_w = __shfl_sync(0xffffffffu, hd == 0, 0);
+        const bool skip_e = __shfl_sync(0xffffffffu, hd == 1, 31);
+        const bool skip_s = __shfl_sync(0xffffffffu, vd == 2, 0);
+        const bool skip_n = __shfl_sync(0xffffffffu, vd == 3, 0);
+        // chunk q of a level's 58: 0..9 e own row from c0w-4, 10..17 e row
+        // j-1, 18..25 e row j+1, 26..41 rt (two float2 each), 42..57 x (two
+        // doubles each); lane l copies chunks l and l + 32
+        auto chunk = [&](int q, const char *&src, int &dst, long long &adv, bool &iss) {
+            const char *base;
+            long long stride;
+            bool skip = false, in_range = true;
+            if (q < 10) {
+                const int sc0 = c0w - 4 + 4 * q;
+                in_range = sc0 >= 0 && sc0 + 4 <= nc;
+                base = reinterpret_cast<const char *>(e + sc0);
+                stride = 4ll * nc;
+                dst = kTrE + 4 * q;
+                skip = (q == 0 && skip_w) || (q == 9 && skip_e);
+            } else if (q < 26) {
+                const bool south = q < 18;
+                const int sc0 = c0w + (south ? -n : n) + 4 * (south ? q - 10 : q - 18);
+                in_range = sc0 >= 0 && sc0 + 4 <= nc;
+                base = reinterpret_cast<const char *>(e + sc0);
+                stride = 4ll * nc;
+                dst = (south ? kTrJm : kTrJp) + 4 * (south ? q - 10 : q - 18);
+                skip = south ? skip_s : skip_n;
+            } else if (q < 42) {
+                base = reinterpret_cast<const char *>(rt + c0w + 2 * (q - 26));
+                stride = 8ll * nc;
+                dst = kTrR + 4 * (q - 26);
+            } else {
+                base = reinterpret_cast<const char *>(x + c0w + 2 * (q - 42));
+                stride = 8ll * nc;
+                dst = kTrX + 4 * (q - 42);
+            }
+            iss = q < 58 && in_range && !skip;
+            src = iss ? base : reinterpret_cast<const char *>(e);  // never read when !iss
+            adv = iss ? stride : 0;
+        };
+        const char *pa, *pb;
+        int da, db;
+        long long aa, ab;
+        bool ia, ib;
+        chunk(lane, pa, da, aa, ia);
+        chunk(lane + 32, pb, db, ab, ib);
+        const float *ph = e + hc, *pv = e + vc;
+        const int hdst = kTrE + (hd == 0 ? 3 : 36);
+        const int vdst = (vd == 2 ? kTrJm : kTrJp) + lane;
+        float *wring = ring + warp * kTrSlot;
+        constexpr int kStride = (kBlk / 32) * kTrSlot;  // floats between ring slots
+        int issued = 0;
+        auto issue = [&]() {  // the next level into its slot (an empty group past the top)
+            if (issued < nz) {
+                float *w = wring + (issued % kTR) * kStride;
+                if (ia) cp_async16(w + da, reinterpret_cast<const float *>(pa), 16);
+                if (ib) cp_async16(w + db, reinterpret_cast<const float *>(pb), 16);
+                if (hd >= 0) cp_async(w + hdst, ph, true);
+                if (vd >= 0) cp_async(w + vdst, pv, true);
+                pa += aa;
+                pb += ab;
+                ph += nc;
+                pv += nc;
+            }
+            ++issued;
+            cp_async_commit();
+        };
+#pragma unroll 1
+        for (int j = 0; j < kTR - 1; ++j) issue();
+        float colsum = 0.f, magsum = 0.f, esum = 0.f;
+        ff flux_lo = {0.f, 0.f};
+        cp_async_wait<kTR - 2>();
+        __syncwarp();
+        float e0 = wring[kTrE + 4 + lane];
+#pragma unroll 1
+        for (int k = 0; k < nz; ++k) {
+            // levels k and k + 1 complete: at most kTR - 2 groups pending
+            __syncwarp();
+            issue();
+            cp_async_wait<kTR - 2>();
+            __syncwarp();
+            const float *sk = wring + (k % kTR) * kStride;
+            const float *sn1 = wring + ((k + 1) % kTR) * kStride;
+            const float ep = k + 1 < nz ? sn1[kTrE + 4 + lane] : 0.f;
+            const float2 rv = reinterpret_cast<const float2 *>(sk + kTrR)[lane];
+            const double xv = reinterpret_cast<const double *>(sk + kTrX)[lane];
+            const TrackOut to = track_level(tc, e0, ep, sk[kTrE + 3 + lane], sk[kTrE + 5 + lane],
+                                            sk[kTrJm + lane], sk[kTrJp + lane], Vh[k], gh[k + 1],
+                                            rv, xv, flux_lo, colsum, magsum, esum);
+            const size_t o = size_t(k) * nc;
+            __stcs(rt + o + c, make_float2(to.nh, to.nl));
+            r32[o + c] = to.nh;
+            __stcs(x + o + c, to.x);
+            e0 = ep;
+        }
+        cp_async_wait<0>();
         acc = double(colsum);
         acc2 = double(magsum);
         acc3 = double(esum);
@@ -2309,8 +2518,16 @@ cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<flo
 cudaError_t launch_ir_track(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                             const Item *items, int nitems, const double *scale, const int *sel,
                             int nmembers, int max_nz, double *partials, double *partials2,
-                            double *partials3) {
+                            double *partials3, bool aligned) {
     if (nitems <= 0) return cudaSuccess;
+    if (aligned) {
+        const size_t sb = ir_track_stg_smem(max_nz);
+        cudaError_t e = set_smem(k_ir_track_stg, sb);
+        if (e != cudaSuccess) return e;
+        k_ir_track_stg<<<nitems, kBlk, sb, s>>>(L64, L32, items, scale, sel, nmembers, max_nz,
+                                                partials, partials2, partials3);
+        return cudaGetLastError();
+    }
     const size_t bytes = size_t(2 * max_nz + 1) * sizeof(float2);
     cudaError_t e = set_smem(k_ir_track, bytes);
     if (e != cudaSuccess) return e;

@@ -94,10 +94,12 @@ cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<flo
 //   x += e / s;  rt = (rt - A e) s_next / s (double-float);  L32[m].b = hi(rt);
 //   partials[item] = sum of (rt - A e)^2 / s^2, partials2[item] = sum of the
 //   squared magnitudes (|A| |e|)^2 / s^2, partials3[item] = sum of (e / s)^2.
+// aligned: every item's level has n % 32 == 0 (the streams are then staged
+// through a shared-memory ring; the same arithmetic and bits).
 cudaError_t launch_ir_track(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                             const Item *items, int nitems, const double *scale, const int *sel,
                             int nmembers, int max_nz, double *partials, double *partials2,
-                            double *partials3);
+                            double *partials3, bool aligned);
 
 // b = A_P V_k f on every item (FP64 or FP32 output), partial sums of b^2.
 template <typename T>

@@ -1058,9 +1058,11 @@ static void ir_step(Plan &pl) {
                                   pl.partials.as<double>(), 0, pl.active.as<int>(), 2,
                                   pl.partials2.as<double>(), pl.maxnz),
                "ir_residual");
+    bool fine_aligned = true;
+    for (const Problem *p : pl.mem) fine_aligned = fine_aligned && p->lev[0].n % 32 == 0;
     check_cuda(launch_ir_track(s, L64, L32, ui, un, pl.scales.as<double>(), pl.active.as<int>(), M,
                                pl.maxnz, pl.partials.as<double>(), pl.partials2.as<double>(),
-                               pl.partials3.as<double>()),
+                               pl.partials3.as<double>(), fine_aligned),
                "ir_track");
     check_cuda(launch_finalize(s, pl.partials.as<double>(), pl.dfirst.as<int>(), M,
                                pl.norms.as<double>(), 1, nullptr, nullptr),
