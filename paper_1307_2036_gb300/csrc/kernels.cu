@@ -15,6 +15,7 @@
 #include "kernels.hpp"
 
 #include <map>
+#include <type_traits>
 #include <mutex>
 
 namespace ells {
@@ -304,6 +305,25 @@ __device__ __forceinline__ void cp_async16(float *smem, const float *gmem, int n
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes)
                  : "memory");
+}
+
+// the same copy issued only where p holds, as a predicated instruction (no
+// branch around it)
+__device__ __forceinline__ void cp_async16_if(float *smem, const float *gmem, bool p) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n"
+        " @q cp.async.cg.shared.global [%0], [%1], 16, 16;\n}\n" ::"r"(s),
+        "l"(gmem), "r"(int(p))
+        : "memory");
+}
+__device__ __forceinline__ void cp_async4_if(float *smem, const float *gmem, bool p) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n"
+        " @q cp.async.ca.shared.global [%0], [%1], 4, 4;\n}\n" ::"r"(s),
+        "l"(gmem), "r"(int(p))
+        : "memory");
 }
 
 // wait until at most n (a constant after unrolling) copy groups are pending
@@ -597,23 +617,19 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
 
     auto issue = [&](int slot) {
         const int so = slot * (kTT / 32) * kSlotF;
-        if (ia) cp_async16(sa + so, pa, na);
+        cp_async16_if(sa + so, pa, ia);
         pa += adva;
-        if (ib) cp_async16(sb2 + so, pb, nb);
+        cp_async16_if(sb2 + so, pb, ib);
         pb += advb;
-        if (ic) cp_async16(sc + so, pc, ncb);
+        cp_async16_if(sc + so, pc, ic);
         pc += advc;
         if (warp_fb) {
             if (ALN) {
                 float *w = wring + so;
-                if (fh) {
-                    cp_async(w + hdst, ph_b, true);
-                    cp_async(w + kLvF + hdst, ph_t, true);
-                }
-                if (fv) {
-                    cp_async(w + vdst, pv_b, true);
-                    cp_async(w + kLvF + vdst, pv_t, true);
-                }
+                cp_async4_if(w + hdst, ph_b, fh);
+                cp_async4_if(w + kLvF + hdst, ph_t, fh);
+                cp_async4_if(w + vdst, pv_b, fv);
+                cp_async4_if(w + kLvF + vdst, pv_t, fv);
             } else {
                 cp_async(fbt + (slot * 4 + 0) * kTT, ph_b, fh);
                 cp_async(fbt + (slot * 4 + 1) * kTT, pv_b, fv);
@@ -647,15 +663,16 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     float *fpp = un + (h ? top0 : 0) + cA;
     const long long fadv = h ? -(long long)nc : (long long)nc;
     const int nblk = m / FR;
-#pragma unroll 1
-    for (int kb = 0; kb < nblk; ++kb) {
-        const bool last = kb == nblk - 1;
+    // one block of FR steps; LAST (the block that ends at the meeting step) is
+    // a compile-time constant, so the other blocks carry none of its tests
+    auto fwd_block = [&](int kb, auto LAST) {
+        constexpr bool last = decltype(LAST)::value;
         if (active) cpt[kb * kTT + tid] = ratio;
 #pragma unroll
         for (int j = 0; j < FR; ++j) {
             const int s = kb * FR + j;
             __syncwarp();
-            if (!last) {
+            if constexpr (!last) {
                 issue((j + FR - 1) % FR);
                 cp_async_wait<FR - 2>();
             } else {
@@ -717,7 +734,10 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             lo = hi;
             lo_g = hi_g;
         }
-    }
+    };
+#pragma unroll 1
+    for (int kb = 0; kb < nblk - 1; ++kb) fwd_block(kb, std::false_type{});
+    fwd_block(nblk - 1, std::true_type{});
     // meeting of the halves: x_{m-1} and x_m from the two last equations, per
     // column, from this lane's and the partner lane's last pivots
     float2 x;
@@ -757,7 +777,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     const long long advk = nbk ? (upw ? (long long)nc : -(long long)nc) : 0;
     float *sbk = wring + 32 * brow + 4 * (lane & 7);
     auto issue_back = [&](int slot) {
-        if (nbk) cp_async16(sbk + slot * kStride, pbk, nbk);
+        cp_async16_if(sbk + slot * kStride, pbk, nbk != 0);
         pbk += advk;
         cp_async_commit();
     };
@@ -765,12 +785,15 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
     for (int j = 0; j < FR - 1; ++j) issue_back(j);
     float *uo_p = un + size_t(h ? m : m - 1) * snc + cA;
     const long long uadv = h ? (long long)nc : -(long long)nc;
-#pragma unroll 1
-    for (int kb = nblk - 1; kb >= 0; --kb) {
+    // one block of FR steps, from the middle out; FIRST (the block holding the
+    // meeting step, whose x is already known) and LAST (the outermost block)
+    // are compile-time constants
+    auto back_block = [&](int kb, auto FIRST, auto LAST) {
+        constexpr bool first = decltype(FIRST)::value, last = decltype(LAST)::value;
         float2 cpr[FR];
         {
             float2 rt = active ? cpt[kb * kTT + tid] : f2(0.f);
-            float2 l0 = kb == 0 ? f2(0.f) : __fmul2_rn(A, f2(VGh[kb * FR - 1].y));
+            float2 l0 = last ? f2(0.f) : __fmul2_rn(A, f2(VGh[kb * FR - 1].y));
 #pragma unroll
             for (int j = 0; j < FR; ++j) {
                 const int s = kb * FR + j;
@@ -784,13 +807,11 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
         }
         unsigned fv[2 * FR];  // TM: f' of the block's steps, both columns of the pair
         if constexpr (TM) tm_ld<FR>(tm + 2u * unsigned(kb * FR), fv);
-        const bool last = kb == 0;
 #pragma unroll
         for (int jj = FR - 1; jj >= 0; --jj) {
-            const int s = kb * FR + jj;
             const int step = FR - 1 - jj;  // position within this block, from the middle out
             __syncwarp();
-            if (!last) {
+            if constexpr (!last) {
                 issue_back((step + FR - 1) % FR);
                 cp_async_wait<FR - 1>();
             } else {
@@ -805,7 +826,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
             else
                 fk = lds2(sk + 32 * h + 2 * p);
             const float2 uo = zero ? f2(0.f) : lds2(sk + 64 + 32 * h + 2 * p);
-            if (s != m - 1) x = __ffma2_rn(cpr[jj], x, fk);
+            if (!first || jj != FR - 1) x = __ffma2_rn(cpr[jj], x, fk);
             const float2 un2 = __ffma2_rn(f2(rho), x, uo);
             // every column is written, the iterate carried over where !upd
             if (active)
@@ -813,6 +834,14 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
                        make_float2(updA ? un2.x : uo.x, updB ? un2.y : uo.y));
             uo_p += uadv;
         }
+    };
+    if (nblk == 1) {
+        back_block(0, std::true_type{}, std::true_type{});
+    } else {
+        back_block(nblk - 1, std::true_type{}, std::false_type{});
+#pragma unroll 1
+        for (int kb = nblk - 2; kb >= 1; --kb) back_block(kb, std::false_type{}, std::false_type{});
+        back_block(0, std::false_type{}, std::true_type{});
     }
     cp_async_wait<0>();
     if (TM) {
