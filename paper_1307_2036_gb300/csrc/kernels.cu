@@ -1368,14 +1368,11 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
         if (k < nz) {
             const size_t o = size_t(k) * snc;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (iq[r]) cp_async16(sl + dq[r], pq[r] + o, 16);
-            if (fa >= 0) cp_async(sl + pa, u + o + fa, true);
-            if (fb2 >= 0) cp_async(sl + pb, u + o + fb2, true);
-            if (fs0 >= 0) {
-                cp_async(sl + ps, u + o + fs0, true);
-                cp_async(sl + ps + 1, u + o + fs1, true);
-            }
+            for (int r = 0; r < 4; ++r) cp_async16_if(sl + dq[r], pq[r] + o, iq[r]);
+            cp_async4_if(sl + pa, u + o + fa, fa >= 0);
+            cp_async4_if(sl + pb, u + o + fb2, fb2 >= 0);
+            cp_async4_if(sl + ps, u + o + fs0, fs0 >= 0);
+            cp_async4_if(sl + ps + 1, u + o + fs1, fs0 >= 0);
         }
         cp_async_commit();
     };
@@ -1968,10 +1965,10 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
         auto issue = [&]() {  // the next level into its slot (an empty group past the top)
             if (issued < nz) {
                 float *w = wring + (issued % kTR) * kStride;
-                if (ia) cp_async16(w + da, reinterpret_cast<const float *>(pa), 16);
-                if (ib) cp_async16(w + db, reinterpret_cast<const float *>(pb), 16);
-                if (hd >= 0) cp_async(w + hdst, ph, true);
-                if (vd >= 0) cp_async(w + vdst, pv, true);
+                cp_async16_if(w + da, reinterpret_cast<const float *>(pa), ia);
+                cp_async16_if(w + db, reinterpret_cast<const float *>(pb), ib);
+                cp_async4_if(w + hdst, ph, hd >= 0);
+                cp_async4_if(w + vdst, pv, vd >= 0);
                 pa += aa;
                 pb += ab;
                 ph += nc;
