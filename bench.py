@@ -807,7 +807,7 @@ def run_serving(torch, stream, count, rate=200.0, low_count=1000, low_rate=60.0,
 
 
 # bumped whenever the finest-level smoother kernel changes (invalidates traffic)
-KERNEL_REV = "smooth-v10-twisted-pairs"
+KERNEL_REV = "smooth-v11-predicated-copies"
 
 
 def main():
