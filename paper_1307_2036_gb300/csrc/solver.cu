@@ -1491,18 +1491,37 @@ static ellsolve_status level_op(Problem &p, int level, int op, const void *a, co
     return ELLSOLVE_OK;
 }
 
-// Time `run` (one launch sequence) after a warm-up: mean ms of three.
+// Time `run` (one launch sequence) after a warm-up: the median of seven runs,
+// each between its own pair of events, so that a gap in which the GPU waits
+// for the host (a short launch enqueued late) or a disturbance of one run
+// does not decide the choice.
 template <typename F>
-double time_ms(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, F run) {
-    run();
-    check_cuda(cudaEventRecord(e0, s), "record");
-    const int reps = 3;
-    for (int r = 0; r < reps; ++r) run();
-    check_cuda(cudaEventRecord(e1, s), "record");
-    check_cuda(cudaEventSynchronize(e1), "sync");
-    float ms = 0.f;
-    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
-    return double(ms) / reps;
+double time_ms(cudaStream_t s, cudaEvent_t, cudaEvent_t, F run) {
+    constexpr int reps = 7;
+    cudaEvent_t ev[2 * reps] = {};
+    double t[reps];
+    try {
+        for (auto &e : ev) check_cuda(cudaEventCreate(&e), "event");
+        run();
+        for (int r = 0; r < reps; ++r) {
+            check_cuda(cudaEventRecord(ev[2 * r], s), "record");
+            run();
+            check_cuda(cudaEventRecord(ev[2 * r + 1], s), "record");
+        }
+        check_cuda(cudaEventSynchronize(ev[2 * reps - 1]), "sync");
+        for (int r = 0; r < reps; ++r) {
+            float ms = 0.f;
+            check_cuda(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]), "elapsed");
+            t[r] = ms;
+        }
+    } catch (...) {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        throw;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    std::sort(t, t + reps);
+    return t[reps / 2];
 }
 
 }  // namespace ells
