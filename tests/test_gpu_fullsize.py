@@ -6,7 +6,7 @@ graph and the autotuned smoother, to relative residual 1e-5.
 The oracle cannot repeat the whole solve at this size in seconds, so it checks
 the result through properties that hold at any size:
   * its own FP64 residual of the returned solution meets the tolerance and
-    agrees with the residual the library reports;
+    agrees with the residual the library reports (the tracked one) to 1e-6;
   * the library's FP64 operator applied to that solution equals the oracle's,
     in relative L2 and on a sample of single cells, within 16x the oracle's own
     rounding sensitivity (A x cancels for a converged x);
@@ -52,7 +52,14 @@ def test_sphere512_solve_meets_tolerance_in_oracle_residual(oracle_mod):
     rr = og.residual(b, xh)
     rel = np.linalg.norm(rr) / np.linalg.norm(b)
     assert rel <= RTOL
-    assert abs(rel - res.rel_residual) <= 1e-3 * rel
+    # the reported residual is the tracked one (double-float updates with a
+    # rounding bound that keeps it within 0.1% of the true one, else an FP64
+    # recomputation).  Measured: 3.1e-9 relative; the bar is 1e-6, far inside
+    # the bound, so that a tracking error well below 0.1% is still caught
+    agree = abs(rel - res.rel_residual) / rel
+    print(f"reported residual {res.rel_residual:.6e}, oracle FP64 residual {rel:.6e}, "
+          f"relative difference {agree:.2e}")
+    assert agree <= 1e-6
     ya = og.apply(xh)
     # A x of a converged solution cancels (A x ~ b while the vertical terms are
     # large), so two correct FP64 evaluations differ by ~eps |A| |x|: the bound
