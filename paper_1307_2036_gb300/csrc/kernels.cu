@@ -307,6 +307,21 @@ __device__ __forceinline__ void cp_async16(float *smem, const float *gmem, int n
                  : "memory");
 }
 
+// Programmatic dependent launch of the small-level kernels.  A kernel launched
+// with the programmatic-serialisation attribute may start while the kernel
+// before it in the stream is still running, once that one has let its
+// dependents launch (pdl_trigger); it must not read or write data the previous
+// kernel touches before pdl_wait returns, which happens when that kernel has
+// completed and its writes are visible.  Without the attribute pdl_wait
+// returns at once, and pdl_trigger has no effect on a dependent launched
+// without it.  So only the set-up that reads constant data (descriptors,
+// geometry, radial coefficients, tensor-memory allocation) overlaps the
+// previous kernel.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // the same copy issued only where p holds, as a predicated instruction (no
 // branch around it)
 __device__ __forceinline__ void cp_async16_if(float *smem, const float *gmem, bool p) {
@@ -805,7 +820,7 @@ __global__ void __launch_bounds__(kTT) k_smooth_tw(const Lv<float> *__restrict__
                 l0 = h1;
             }
         }
-        unsigned fv[2 * FR];  // TM: f' of the block's steps, both columns of the pair
+        [[maybe_unused]] unsigned fv[2 * FR];  // TM: f' of the block's steps, both columns
         if constexpr (TM) tm_ld<FR>(tm + 2u * unsigned(kb * FR), fv);
 #pragma unroll
         for (int jj = FR - 1; jj >= 0; --jj) {
@@ -900,6 +915,7 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
     const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
     constexpr bool zero = ZERO == 1;
     const unsigned half = unsigned(stg_tmem_half(max_nz));
+    pdl_trigger();
     if (warp == 0) tm_alloc(tm_sh, 2u * half);
     const float *__restrict__ u = d.u[it.in];
     float *__restrict__ un = d.u[it.out];
@@ -925,6 +941,11 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
             if (nbr.w != c + n) { vd = 3; vc = nbr.w; }
         }
     }
+    for (int i = tid; i < m; i += 32 * kStgW) {
+        VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
+        GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
+    }
+    pdl_wait();  // the iterate and right-hand side come from the kernels before
     // staging: lane l copies chunk l (and lanes 0, 1 chunks 32, 33) of the
     // levels k = w, w + 8, ... of its warp w; chunk r: 0..9 own row c0w-4..,
     // 10..17 b, 18..25 row j-1, 26..33 row j+1
@@ -945,10 +966,6 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
     if (vd >= 0)
         for (int k = warp; k < nz; k += kStgW) cp_async(vb + k * 32 + lane, u + k * snc + vc, true);
     cp_async_commit();
-    for (int i = tid; i < m; i += 32 * kStgW) {
-        VP[i] = make_float2(d.V[i], d.V[nz - 1 - i]);
-        GH[i] = make_float2(d.g[i + 1], d.g[nz - 1 - i]);
-    }
     cp_async_wait<0>();
     tm_fence_before();
     __syncthreads();
@@ -1133,6 +1150,7 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
     constexpr int R = restrict_ring<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw) + threadIdx.x;  // ring[slot][16][kBlk]
+    pdl_trigger();
     const Item it = items[blockIdx.x];
     const Lv<T> &d = L[it.lv];
     const Lv<T> &dc = L[it.lv + 1];
@@ -1174,6 +1192,7 @@ __global__ void __launch_bounds__(kBlk) k_restrict_resid(const Lv<T> *__restrict
         for (int e = 0; e < 8; ++e) cp_async(sl + (8 + e) * kBlk, u + o + ext[e], ok);
         cp_async_commit();
     };
+    pdl_wait();  // u and b come from the kernels before
 #pragma unroll 1
     for (int k = kb; k < kb + R - 1; ++k) issue(k);
     T u0[4], um[4];
@@ -1459,6 +1478,7 @@ constexpr int kPB = 8;
 template <typename T>
 __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ L,
                                                       const Item *__restrict__ items, int mode) {
+    pdl_trigger();
     const Item it = items[blockIdx.x];
     const Lv<T> &d = L[it.lv];
     const Lv<T> &dc = L[it.lv + 1];
@@ -1475,6 +1495,7 @@ __global__ void __launch_bounds__(kBlk) k_prolong_add(const Lv<T> *__restrict__ 
     // levels [kb, ke): one chunk per blockIdx.y
     const int KC = (nz + int(gridDim.y) - 1) / int(gridDim.y);
     const int kb = int(blockIdx.y) * KC, ke = min(nz, kb + KC);
+    pdl_wait();  // the coarse correction and the fine iterate come from the kernels before
     for (int k0 = kb; k0 < ke; k0 += kPB) {
         T cx[kPB], cy[kPB], cz[kPB], cw[kPB], fv[kPB];
 #pragma unroll
@@ -2276,6 +2297,26 @@ __global__ void k_cg_scalars(double *scalars, const double *sums, int op) {
 // Opt a kernel in to more than 48 KB of dynamic shared memory (once per
 // kernel and size; the attribute is per function, so the cache is keyed on
 // the kernel's address).
+// A launch, with programmatic dependent launch when pdl (see pdl_trigger).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// launches this small overlap their set-up with the kernel before them
+constexpr int kPdlItems = 4 * 152;
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
     static std::mutex mu;
@@ -2391,8 +2432,8 @@ static cudaError_t launch_stg_z(cudaStream_t s, const Lv<float> *L, const Item *
     if (cap > bytes) bytes = cap;
     cudaError_t e = set_smem(k_smooth_stg<Z>, bytes);
     if (e != cudaSuccess) return e;
-    k_smooth_stg<Z><<<unsigned(nitems) * 4u, 32 * kStgW, bytes, s>>>(L, items, rho, max_nz);
-    return cudaGetLastError();
+    return launch_k(true, k_smooth_stg<Z>, dim3(unsigned(nitems) * 4u), dim3(32 * kStgW), bytes, s,
+                    L, items, rho, max_nz);
 }
 
 cudaError_t launch_smooth_stg(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
@@ -2445,8 +2486,7 @@ cudaError_t launch_restrict_resid(cudaStream_t s, const Lv<T> *L, const Item *it
     cudaError_t e = set_smem(k_restrict_resid<T>, bytes);
     if (e != cudaSuccess) return e;
     const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz, chunk_blocks)));
-    k_restrict_resid<T><<<grid, kBlk, bytes, s>>>(L, items);
-    return cudaGetLastError();
+    return launch_k(nitems < kPdlItems, k_restrict_resid<T>, grid, dim3(kBlk), bytes, s, L, items);
 }
 
 cudaError_t launch_restrict_rows(cudaStream_t s, const Lv<float> *L, const Item *items,
@@ -2471,8 +2511,8 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
                                int mode, int max_nz, int chunk_blocks) {
     if (nitems <= 0) return cudaSuccess;
     const dim3 grid(unsigned(nitems), unsigned(level_chunks(nitems, max_nz, chunk_blocks)));
-    k_prolong_add<T><<<grid, kBlk, 0, s>>>(L, items, mode);
-    return cudaGetLastError();
+    return launch_k(nitems < kPdlItems, k_prolong_add<T>, grid, dim3(kBlk), size_t(0), s, L, items,
+                    mode);
 }
 
 // Self-test of the integer-arithmetic conversions against the hardware ones
