@@ -342,6 +342,10 @@ def run_ours(args, rank, world, local_rank):
     ev_out = [torch.cuda.Event() for _ in range(2)]
     e2e_cycles = 0
     K = args.steps
+    cin = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    cout = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(K)]
     h0.record(stream)
     h2d.wait_event(h0)
     with torch.cuda.stream(h2d):
@@ -353,7 +357,9 @@ def run_ours(args, rank, world, local_rank):
             if i >= 1:
                 h2d.wait_event(ev_solved[1 - j])
             with torch.cuda.stream(h2d):
+                cin[i][0].record(h2d)
                 fd[1 - j].copy_(f_host, non_blocking=True)
+                cin[i][1].record(h2d)
                 ev_in[1 - j].record(h2d)
         stream.wait_event(ev_in[j])
         if i >= 2:
@@ -367,7 +373,9 @@ def run_ours(args, rank, world, local_rank):
         ev_solved[j].record(stream)
         d2h.wait_event(ev_solved[j])
         with torch.cuda.stream(d2h):
+            cout[i][0].record(d2h)
             x_host.copy_(xd[j], non_blocking=True)
+            cout[i][1].record(d2h)
             ev_out[j].record(d2h)
     for j in range(min(2, K)):
         stream.wait_event(ev_out[j])
@@ -375,6 +383,9 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms_e2e = h0.elapsed_time(h1)
     e2e_solve_ms = sum(a.elapsed_time(b) for a, b in solve_ev) / max(1, len(solve_ev))
+    # the copies' own durations inside the loop (beside the solves)
+    cin_ms = [a.elapsed_time(b) for a, b in cin[:max(0, K - 1)]]
+    cout_ms = [a.elapsed_time(b) for a, b in cout[:K]]
     del fd, xd
 
     if dist is not None:
@@ -441,7 +452,10 @@ def run_ours(args, rank, world, local_rank):
                           "input and step i-1's output move during step i's solve",
                 "copy_gbs_alone": {"h2d": copy_gbs[0], "d2h": copy_gbs[1]},
                 "host_cpus": host_cpus,
-                "solve_ms_in_loop": e2e_solve_ms},
+                "solve_ms_in_loop": e2e_solve_ms,
+                "copy_ms_in_loop": {
+                    "h2d": sum(cin_ms) / len(cin_ms) if cin_ms else None,
+                    "d2h": sum(cout_ms) / len(cout_ms) if cout_ms else None}},
         "clocks": clocks,
         "gpu_launches": int(launches),
     }

@@ -14,9 +14,10 @@
 // against the large vertical coupling.
 #include "kernels.hpp"
 
+#include <cstring>
 #include <map>
-#include <type_traits>
 #include <mutex>
+#include <type_traits>
 
 namespace ells {
 namespace {
@@ -1700,7 +1701,8 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
 }
 
 // ---------------------------------------------------------------------------
-// Tracked refinement step (members with sel == 1).  With x the FP64 iterate,
+// Tracked refinement step (members with sel 1, or 3 when x = 0: x is then not
+// read, x + e / s formed as 0 + e / s).  With x the FP64 iterate,
 // e the inner correction (FP32, scaled by s = 2^-k) and rt = r s the stored
 // scaled residual (double-float):
 //     x  += e / s                       (one FP64 add)
@@ -1790,7 +1792,9 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
     extern __shared__ float2 vg_sh[];  // (V_k hi, lo) [max_nz], (g_k hi, lo) [max_nz + 1]
     float2 *Vh = vg_sh, *gh = vg_sh + max_nz;
     const Item it = items[blockIdx.x];
-    if (sel[it.lv] != 1) return;
+    const int mode = sel[it.lv];  // 1 tracked, 3 tracked with x = 0 (not read)
+    if (mode != 1 && mode != 3) return;
+    const bool x0 = mode == 3;
     const Lv<double> &d = L64[it.lv];
     const int nz = d.nz, nc = d.ncol;
     for (int k = threadIdx.x; k <= nz; k += kBlk) {
@@ -1833,7 +1837,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track(const Lv<double> *__restrict_
                 es[j] = __ldg(row + col.nb.z);
                 en[j] = __ldg(row + col.nb.w);
                 rv[j] = __ldcs(rt + o + c);  // x and rt: not needed before the next step
-                xv[j] = __ldcs(x + o + c);
+                xv[j] = x0 ? 0.0 : __ldcs(x + o + c);
             }
 #pragma unroll
             for (int j = 0; j < kTB; ++j) {
@@ -1899,7 +1903,9 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
     float *ring = reinterpret_cast<float *>(smem_raw + (size_t(2 * max_nz + 1) * sizeof(float2) +
                                                        15) / 16 * 16);
     const Item it = items[blockIdx.x];
-    if (sel[it.lv] != 1) return;
+    const int mode = sel[it.lv];  // 1 tracked, 3 tracked with x = 0 (not read)
+    if (mode != 1 && mode != 3) return;
+    const bool x0 = mode == 3;
     const Lv<double> &d = L64[it.lv];
     const int nz = d.nz, nc = d.ncol, n = d.n;
     for (int k = threadIdx.x; k <= nz; k += kBlk) {
@@ -1966,6 +1972,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
                 base = reinterpret_cast<const char *>(x + c0w + 2 * (q - 42));
                 stride = 8ll * nc;
                 dst = kTrX + 4 * (q - 42);
+                skip = x0;  // x = 0 is not read
             }
             iss = q < 58 && in_range && !skip;
             src = iss ? base : reinterpret_cast<const char *>(e);  // never read when !iss
@@ -2016,7 +2023,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
             const float *sn1 = wring + ((k + 1) % kTR) * kStride;
             const float ep = k + 1 < nz ? sn1[kTrE + 4 + lane] : 0.f;
             const float2 rv = reinterpret_cast<const float2 *>(sk + kTrR)[lane];
-            const double xv = reinterpret_cast<const double *>(sk + kTrX)[lane];
+            const double xv = x0 ? 0.0 : reinterpret_cast<const double *>(sk + kTrX)[lane];
             const TrackOut to = track_level(tc, e0, ep, sk[kTrE + 3 + lane], sk[kTrE + 5 + lane],
                                             sk[kTrJm + lane], sk[kTrJp + lane], Vh[k], gh[k + 1],
                                             rv, xv, flux_lo, colsum, magsum, esum);
@@ -2615,6 +2622,31 @@ cudaError_t launch_finalize(cudaStream_t s, const double *partials, const int *f
     if (nmembers <= 0) return cudaSuccess;
     k_finalize<<<nmembers, 256, 0, s>>>(partials, first, out, op, scale_out, counts);
     return cudaGetLastError();
+}
+
+// Small host data (per-solve descriptors, scales, flags) written to the device
+// by a kernel whose parameter carries it, instead of a host-to-device copy: a
+// copy would queue on the copy engine behind a large transfer the caller may
+// have in flight (the next right-hand side), and the solve would wait for it.
+struct SmallBlob {
+    unsigned n;
+    unsigned char b[kBlobBytes];
+};
+__global__ void __launch_bounds__(256) k_put_bytes(unsigned char *__restrict__ dst, SmallBlob blob) {
+    for (unsigned i = threadIdx.x; i < blob.n; i += blockDim.x) dst[i] = blob.b[i];
+}
+
+int launch_put_bytes(cudaStream_t s, void *dst, const void *src, size_t n) {
+    int launches = 0;
+    for (size_t off = 0; off < n; off += kBlobBytes) {
+        SmallBlob blob;
+        blob.n = unsigned(n - off < size_t(kBlobBytes) ? n - off : size_t(kBlobBytes));
+        std::memcpy(blob.b, static_cast<const unsigned char *>(src) + off, blob.n);
+        k_put_bytes<<<1, 256, 0, s>>>(static_cast<unsigned char *>(dst) + off, blob);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+        ++launches;
+    }
+    return launches;
 }
 
 cudaError_t launch_copy_doubles(cudaStream_t s, const double *src, double *dst, int n) {

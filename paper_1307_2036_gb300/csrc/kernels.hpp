@@ -89,7 +89,8 @@ cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<f
 cudaError_t launch_ir_update(cudaStream_t s, const Lv<double> *L64, const Lv<float> *L32,
                              const Item *items, int nitems, const double *scale,
                              const int *sel, int want, double *partials3);
-// Tracked refinement step for members with sel[m] == 1 (scale[m] = s,
+// Tracked refinement step for members with sel[m] == 1, or 3 when their x is
+// zero and is not read (the first step from x = 0) (scale[m] = s,
 // scale[nmembers + m] = s_next, e = L32[m].u[item.in], rt = L64[m].aux):
 //   x += e / s;  rt = (rt - A e) s_next / s (double-float);  L32[m].b = hi(rt);
 //   partials[item] = sum of (rt - A e)^2 / s^2, partials2[item] = sum of the
@@ -112,6 +113,12 @@ cudaError_t launch_form_rhs(cudaStream_t s, const Lv<T> *L, const Item *items, i
 // scale_out != null.
 // dst[i] = src[i], i < n, by one block of SM threads (dst may be mapped host memory)
 cudaError_t launch_copy_doubles(cudaStream_t s, const double *src, double *dst, int n);
+
+// n bytes of host data at src to device memory at dst, carried in the
+// parameters of kernel launches on s (kBlobBytes per launch) rather than by a
+// copy engine; returns the number of launches, or -1 on a launch error.
+constexpr int kBlobBytes = 2048;
+int launch_put_bytes(cudaStream_t s, void *dst, const void *src, size_t n);
 
 cudaError_t launch_finalize(cudaStream_t s, const double *partials, const int *first, int nmembers,
                             double *out, int op, double *scale_out, const double *counts);

@@ -172,7 +172,10 @@ void ellsolve_server_s::run_worker() {
             bool any = false;
             for (MemberRun *r : run) any = any || r->active;
             if (any) ir_advance(*plan, run, false);
-            // retire finished requests
+            // retire finished requests (a request that stopped before any update
+            // gets its x = 0 written first)
+            if (ir_zero_unwritten(*plan, run))
+                check_cuda(cudaStreamSynchronize(plan->mem[0]->stream), "retire sync");
             std::vector<Request *> keep;
             std::lock_guard<std::mutex> lock(mu);
             for (Request *q : active) {

@@ -919,6 +919,12 @@ static double pow2_scale(double norm, size_t N) {
     return std::ldexp(1.0, -std::ilogb(norm / std::sqrt(double(N))));
 }
 
+static void put_bytes(Plan &pl, void *dst, const void *src, size_t n) {
+    const int k = launch_put_bytes(pl.mem[0]->stream, dst, src, n);
+    if (k < 0) check_cuda(cudaGetLastError(), "put_bytes");
+    count(pl, k);
+}
+
 // Outer descriptors: member m's finest FP64 level with u[0] = x_m, b = f_m.
 void ir_bind(Plan &pl, const std::vector<MemberRun *> &run) {
     const int M = int(pl.mem.size());
@@ -934,13 +940,10 @@ void ir_bind(Plan &pl, const std::vector<MemberRun *> &run) {
     cudaStream_t s = pl.mem[0]->stream;
     if (pl.outer64.bytes != M * sizeof(Lv<double>)) pl.outer64.alloc(M * sizeof(Lv<double>));
     if (pl.fine32.bytes != M * sizeof(Lv<float>)) pl.fine32.alloc(M * sizeof(Lv<float>));
-    check_cuda(cudaMemcpyAsync(pl.outer64.p, pl.stage64.data(), M * sizeof(Lv<double>),
-                               cudaMemcpyHostToDevice, s),
-               "outer desc");
-    check_cuda(cudaMemcpyAsync(pl.fine32.p, pl.stage32.data(), M * sizeof(Lv<float>),
-                               cudaMemcpyHostToDevice, s),
-               "fine desc");
-    check_cuda(cudaStreamSynchronize(s), "desc sync");
+    // through kernel parameters, not copies (see launch_put_bytes): a caller's
+    // transfer in flight on the copy engine does not hold up the solve
+    put_bytes(pl, pl.outer64.p, pl.stage64.data(), M * sizeof(Lv<double>));
+    put_bytes(pl, pl.fine32.p, pl.stage32.data(), M * sizeof(Lv<float>));
 }
 
 static void ir_push_state(Plan &pl, const std::vector<MemberRun *> &run) {
@@ -950,15 +953,12 @@ static void ir_push_state(Plan &pl, const std::vector<MemberRun *> &run) {
     for (int m = 0; m < M; ++m) {
         pl.stage_scales[m] = run[m]->scale_cur;
         pl.stage_scales[M + m] = run[m]->scale_next;
-        pl.stage_active[m] = run[m]->active ? run[m]->mode : 0;  // 0 idle, 1 tracked, 2 FP64
+        // 0 idle, 1 tracked, 2 FP64, 3 tracked with x = 0 (the first update writes x)
+        const MemberRun &r = *run[m];
+        pl.stage_active[m] = r.active ? (r.mode == 1 && r.x_zero ? 3 : r.mode) : 0;
     }
-    cudaStream_t s = pl.mem[0]->stream;
-    check_cuda(cudaMemcpyAsync(pl.scales.p, pl.stage_scales.data(), 2 * M * sizeof(double),
-                               cudaMemcpyHostToDevice, s),
-               "scales");
-    check_cuda(cudaMemcpyAsync(pl.active.p, pl.stage_active.data(), M * sizeof(int),
-                               cudaMemcpyHostToDevice, s),
-               "active");
+    put_bytes(pl, pl.scales.p, pl.stage_scales.data(), 2 * M * sizeof(double));
+    put_bytes(pl, pl.active.p, pl.stage_active.data(), M * sizeof(int));
 }
 
 // FP64 residual of members [m0, m1) formed with scale_next, its norm (norms[m])
@@ -999,7 +999,15 @@ void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep
     pl.sync_items();
     for (int m = m0; m < m1; ++m) {
         MemberRun &r = *run[m];
-        if (!keep_x) check_cuda(cudaMemsetAsync(r.x, 0, pl.mem[m]->N * 8, s), "zero x");
+        // x = 0: a tracked member's first update writes x without reading it;
+        // an FP64 member's update reads it, so it is cleared now
+        r.x_zero = false;
+        if (!keep_x) {
+            if (pl.mem[m]->opts.refine == 1)
+                check_cuda(cudaMemsetAsync(r.x, 0, pl.mem[m]->N * 8, s), "zero x");
+            else
+                r.x_zero = true;
+        }
         r.scale_cur = r.scale_next = 1.0;
         r.active = true;
         r.iters = 0;
@@ -1145,6 +1153,7 @@ void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph) {
     for (int m = 0; m < M; ++m) {
         MemberRun &r = *run[m];
         if (!r.active) continue;
+        r.x_zero = false;  // the update wrote x
         r.dx_prev = r.dx_last;
         r.dx_last = pl.host_norms[2 * M + m];
         if (r.iters == 0) r.dx_first = r.dx_last;
@@ -1188,6 +1197,18 @@ void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph) {
         if (!(r.rel > r.rtol) || !std::isfinite(r.rel) || r.iters >= r.maxit || stagnated(r.hist))
             r.active = false;
     }
+}
+
+bool ir_zero_unwritten(Plan &pl, const std::vector<MemberRun *> &run) {
+    bool any = false;
+    for (size_t m = 0; m < run.size(); ++m) {
+        MemberRun &r = *run[m];
+        if (r.active || !r.x_zero) continue;
+        check_cuda(cudaMemsetAsync(r.x, 0, pl.mem[m]->N * 8, pl.mem[0]->stream), "zero x");
+        r.x_zero = false;
+        any = true;
+    }
+    return any;
 }
 
 // Estimate of ||x* - x|| / ||x*|| for a refinement solve from x = 0.  If the
@@ -1246,6 +1267,7 @@ ellsolve_status solve_ir(Plan &pl, const std::vector<const double *> &f,
     if (maxit <= 0)
         for (auto &r : runs) r.active = false;
     while (any()) ir_advance(pl, run, p0.opts.use_graph != 0);
+    ir_zero_unwritten(pl, run);
     check_cuda(cudaStreamSynchronize(s), "solve sync");
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     res.resize(M);

@@ -223,11 +223,18 @@ struct MemberRun {
     double errb = 0.0, magx = 0.0;
     // norms of the first, the one but last and the latest update of x (error estimate)
     double dx_first = 0.0, dx_prev = 0.0, dx_last = 0.0;
+    // x = 0 and not yet written: the first tracked update writes e / s without
+    // reading x (so x is not cleared beforehand); ir_zero_unwritten clears it
+    // for a member that stops before any update
+    bool x_zero = false;
 };
 
 void ir_bind(Plan &pl, const std::vector<MemberRun *> &run);
 void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep_x);
 void ir_advance(Plan &pl, std::vector<MemberRun *> &run, bool use_graph);
+// writes x = 0 (on the plan's stream) for the finished members whose x was
+// never written (no update ran); true when it enqueued any
+bool ir_zero_unwritten(Plan &pl, const std::vector<MemberRun *> &run);
 ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res);
 
 // One line-smoother launch: the twisted FP32 kernel where `rows_ok`, else the
