@@ -1383,8 +1383,8 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
     float *wring = ring + warp * kRsF;
     constexpr int kStride = (kBlk / 32) * kRsF;
 
-    auto issue = [&](int k) {
-        float *sl = wring + (k % kRR) * kStride;
+    auto issue = [&](int k, int slot) {  // slot = k % kRR
+        float *sl = wring + slot * kStride;
         if (k < nz) {
             const size_t o = size_t(k) * snc;
 #pragma unroll
@@ -1397,7 +1397,7 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
         cp_async_commit();
     };
 #pragma unroll
-    for (int k = 0; k < kRR - 1; ++k) issue(k);
+    for (int k = 0; k < kRR - 1; ++k) issue(k, k);
 
     const int o0 = 4 + 2 * lane;  // this lane's child pair in the halo rows
     const float2 A01 = make_float2(c0.A, c1.A), A23 = make_float2(c2.A, c3.A);
@@ -1411,14 +1411,16 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
     float2 u23 = *reinterpret_cast<const float2 *>(wring + kR1 + o0);
     float2 m01 = f2(0.f), m23 = f2(0.f);
     float gk = d.g[0];
-#pragma unroll 1
-    for (int k = 0; k < nz; ++k) {
+    // level k in ring slot j = k % kRR, unrolled over the slots so that the
+    // slot offsets are constants; past the top only the empty copy groups run
+    auto level = [&](int k, int j) {
         __syncwarp();
-        issue(k + kRR - 1);
+        issue(k + kRR - 1, (j + kRR - 1) % kRR);
         cp_async_wait<kRR - 2>();
         __syncwarp();
-        const float *sk = wring + (k % kRR) * kStride;
-        const float *sn = wring + ((k + 1) % kRR) * kStride;
+        if (k >= nz) return;
+        const float *sk = wring + j * kStride;
+        const float *sn = wring + ((j + 1) % kRR) * kStride;
         const float gk1 = d.g[k + 1], Vk = d.V[k];
         float2 p01 = f2(0.f), p23 = f2(0.f);
         if (k + 1 < nz) {
@@ -1460,6 +1462,11 @@ __global__ void __launch_bounds__(kBlk) k_restrict_rows(const Lv<float> *__restr
         u01 = p01;
         u23 = p23;
         gk = gk1;
+    };
+#pragma unroll 1
+    for (int k0 = 0; k0 < nz; k0 += kRR) {
+#pragma unroll
+        for (int j = 0; j < kRR; ++j) level(k0 + j, j);
     }
     cp_async_wait<0>();
 }
