@@ -1997,9 +1997,10 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
         float *wring = ring + warp * kTrSlot;
         constexpr int kStride = (kBlk / 32) * kTrSlot;  // floats between ring slots
         int issued = 0;
-        auto issue = [&]() {  // the next level into its slot (an empty group past the top)
+        // the next level into ring slot `slot` (= issued % kTR), an empty group past the top
+        auto issue = [&](int slot) {
             if (issued < nz) {
-                float *w = wring + (issued % kTR) * kStride;
+                float *w = wring + slot * kStride;
                 cp_async16_if(w + da, reinterpret_cast<const float *>(pa), ia);
                 cp_async16_if(w + db, reinterpret_cast<const float *>(pb), ib);
                 cp_async4_if(w + hdst, ph, hd >= 0);
@@ -2012,22 +2013,24 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
             ++issued;
             cp_async_commit();
         };
-#pragma unroll 1
-        for (int j = 0; j < kTR - 1; ++j) issue();
+#pragma unroll
+        for (int j = 0; j < kTR - 1; ++j) issue(j);
         float colsum = 0.f, magsum = 0.f, esum = 0.f;
         ff flux_lo = {0.f, 0.f};
         cp_async_wait<kTR - 2>();
         __syncwarp();
         float e0 = wring[kTrE + 4 + lane];
-#pragma unroll 1
-        for (int k = 0; k < nz; ++k) {
+        // level k in ring slot j = k % kTR, unrolled over the slots so that the
+        // slot offsets are constants; past the top only the empty groups run
+        auto level = [&](int k, int j) {
             // levels k and k + 1 complete: at most kTR - 2 groups pending
             __syncwarp();
-            issue();
+            issue((j + kTR - 1) % kTR);
             cp_async_wait<kTR - 2>();
             __syncwarp();
-            const float *sk = wring + (k % kTR) * kStride;
-            const float *sn1 = wring + ((k + 1) % kTR) * kStride;
+            if (k >= nz) return;
+            const float *sk = wring + j * kStride;
+            const float *sn1 = wring + ((j + 1) % kTR) * kStride;
             const float ep = k + 1 < nz ? sn1[kTrE + 4 + lane] : 0.f;
             const float2 rv = reinterpret_cast<const float2 *>(sk + kTrR)[lane];
             const double xv = x0 ? 0.0 : reinterpret_cast<const double *>(sk + kTrX)[lane];
@@ -2039,6 +2042,11 @@ __global__ void __launch_bounds__(kBlk) k_ir_track_stg(const Lv<double> *__restr
             r32[o + c] = to.nh;
             __stcs(x + o + c, to.x);
             e0 = ep;
+        };
+#pragma unroll 1
+        for (int k0 = 0; k0 < nz; k0 += kTR) {
+#pragma unroll
+            for (int j = 0; j < kTR; ++j) level(k0 + j, j);
         }
         cp_async_wait<0>();
         acc = double(colsum);
