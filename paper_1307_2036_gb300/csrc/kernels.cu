@@ -1575,7 +1575,7 @@ __device__ __forceinline__ ff split_ff(double d) {
 // ---------------------------------------------------------------------------
 // FP64 outer residual of the iterative refinement.
 // ---------------------------------------------------------------------------
-// MODE 0: general x; 1: x = 0 (r = A V f); 2: x = 0, norm only (r32 untouched)
+// MODE 0: general x; 1: x = 0 (r = A V f)
 template <int MODE>
 __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restrict__ L64,
                                                       const Lv<float> *__restrict__ L32,
@@ -1609,7 +1609,9 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         float2 *__restrict__ rt = reinterpret_cast<float2 *>(d.aux);  // scaled residual
         const float sc = float(scale[it.lv]);  // a power of two: exact in FP32
         const Column<double> col = load_column(d, c);
-        float colsum = 0.f;  // this column's sum of r^2 (only steers the stopping test)
+        // this column's sum of (r s)^2, the scaled values, which stay far from
+        // FP32 underflow and overflow; divided by s^2 (exact) per block
+        float colsum = 0.f;
         if (MODE == 1) {
             // x = 0: r = b = A_P V_k f in double-float (f split into hi + lo
             // with one FP64 subtraction); r32 = its high part, scaled
@@ -1630,25 +1632,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                         const float h = __fmul_rn(bk.hi, sc);
                         rt[o] = make_float2(h, __fmul_rn(bk.lo, sc));
                         r32[o] = h;
-                        colsum = __fmaf_rn(bk.hi, bk.hi, colsum);
-                    }
-                }
-            }
-        } else if (MODE == 2) {
-            // x = 0, the norm of b only (fixes the scale), in FP32
-            const float A32 = e32.area[c];
-            constexpr int B = 8;
-            for (int k0 = 0; k0 < nz; k0 += B) {
-                double fv[B];
-#pragma unroll
-                for (int j = 0; j < B; ++j) fv[j] = __ldg(f + size_t(min(k0 + j, nz - 1)) * nc + c);
-#pragma unroll
-                for (int j = 0; j < B; ++j) {
-                    const int k = k0 + j;
-                    if (k < nz) {
-                        const float rf =
-                            __fmul_rn(__fmul_rn(A32, __ldg(e32.V + k)), f64_to_f32_rn(fv[j]));
-                        colsum = fmaf(rf, rf, colsum);
+                        colsum = __fmaf_rn(h, h, colsum);
                     }
                 }
             }
@@ -1686,7 +1670,7 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
                 const float h = rf * sc;
                 r32[o + c] = h;
                 rt[o + c] = make_float2(h, rl * sc);
-                colsum = fmaf(rf, rf, colsum);
+                colsum = fmaf(h, h, colsum);
                 const float mag = fabsf(f64_to_f32_rn(u0)) *
                                   fmaf(__ldg(e32.V + k), wsum,
                                        2.f * A32 * (__ldg(e32.g + k) + __ldg(e32.g + k + 1)));
@@ -1698,7 +1682,8 @@ __global__ void __launch_bounds__(kBlk) k_ir_residual(const Lv<double> *__restri
         }
         acc = double(colsum);
     }
-    const double t = block_sum(acc);
+    const double sc = scale[it.lv];
+    const double t = block_sum(acc) * (1.0 / (sc * sc));
     if (MODE == 0) {
         __syncthreads();  // block_sum's shared slots are reused
         const double t2 = block_sum(acc2);
@@ -2579,10 +2564,7 @@ cudaError_t launch_ir_residual(cudaStream_t s, const Lv<double> *L64, const Lv<f
                                double *partials, int x_is_zero, const int *sel, int want,
                                double *partials2, int max_nz) {
     if (nitems <= 0) return cudaSuccess;
-    if (x_is_zero == 2)
-        k_ir_residual<2><<<nitems, kBlk, 0, s>>>(L64, L32, items, scale, sel, want, partials,
-                                                 partials2);
-    else if (x_is_zero) {
+    if (x_is_zero) {
         const size_t bytes = size_t(max_nz) * sizeof(float2);
         cudaError_t e = set_smem(k_ir_residual<1>, bytes);
         if (e != cudaSuccess) return e;

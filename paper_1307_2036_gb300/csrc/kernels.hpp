@@ -72,7 +72,7 @@ cudaError_t launch_prolong_add(cudaStream_t s, const Lv<T> *L, const Item *items
 //   as double-float, partials[item] = sum of r^2, partials2[item] = squared
 //   magnitude of |A| |x| (bound on the rounding of the evaluation).
 // x_is_zero: 1 x = 0, so r = A_P V_k f without the stencil (start of a solve;
-// r and its norm only); 2 the same but only the norm (nothing written).
+// r and its norm only).
 // sel: when not null, only members with sel[m] == want take part.  max_nz:
 // the largest nz among the members.
 // Row-staged FP32 residual + restriction; every fine level of the launch has

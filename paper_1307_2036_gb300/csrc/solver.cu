@@ -120,6 +120,7 @@ std::shared_ptr<const Geometry> geometry_for(const ellsolve_grid &g, int coarses
         LevelGeom &L = geo->lev[l];
         L.n = hl.n;
         L.ncol = int(hl.ncol);
+        for (double ar : hl.area) L.area_sq += ar * ar;
         const size_t nc = size_t(hl.ncol);
         std::vector<int4> nb(nc), ps(nc);
         std::vector<double4_32a> tr64(nc);
@@ -282,6 +283,9 @@ void Problem::rebind(double w2, double l2, const double *rl, const double *pc, c
         for (int k = 0; k < nz; ++k) V[k] *= p_cell[k];
     if (!q_face.empty())
         for (int k = 1; k < nz; ++k) G[k] *= q_face[k];
+    double vsq = 0.0;
+    for (int k = 0; k < nz; ++k) vsq += V[k] * V[k];
+    b_unit_norm = std::sqrt(geom->lev[0].area_sq * vsq);
     std::vector<double> gv(nz + 1);
     for (int k = 0; k <= nz; ++k) gv[k] = w2 * l2 * G[k];
     std::vector<float> V32h(V.begin(), V.end()), g32h(gv.begin(), gv.end());
@@ -1008,25 +1012,40 @@ void ir_start(Plan &pl, std::vector<MemberRun *> &run, int m0, int m1, bool keep
             else
                 r.x_zero = true;
         }
-        r.scale_cur = r.scale_next = 1.0;
+        // from x = 0 the residual is b: its first scale is the one that
+        // normalises b for f = 1; with x given, 1 until its residual is known
+        r.scale_cur = r.scale_next =
+            keep_x ? 1.0 : pow2_scale(pl.mem[m]->b_unit_norm, pl.mem[m]->N);
         r.active = true;
         r.iters = 0;
         r.hist.assign(1, 1.0);
         r.dx_first = r.dx_prev = r.dx_last = 0.0;
     }
     ir_push_state(pl, run);
-    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 2);  // the norm only: it fixes the scale
+    // x = 0: b (in double-float, with that scale) and its norm in one pass;
+    // x given: the norm of its residual first, which fixes the scale
+    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
     read_norms(pl, int(pl.mem.size()));
+    bool again = keep_x;
     for (int m = m0; m < m1; ++m) {
         MemberRun &r = *run[m];
         r.bnorm = pl.host_norms[m];
         r.rel = std::isfinite(r.bnorm) ? (r.bnorm > 0 ? 1.0 : 0.0) : r.bnorm;
         if (!(r.bnorm > 0) || !std::isfinite(r.bnorm)) r.active = false;
-        r.scale_cur = r.scale_next = pow2_scale(r.bnorm, pl.mem[m]->N);
+        const double sc = pow2_scale(r.bnorm, pl.mem[m]->N);
+        // A power of two changes no bit of the result; only a right-hand side
+        // whose magnitude puts the scaled b more than 2^20 from unit RMS (the
+        // FP32 range margin) is formed again with its own scale.
+        if (keep_x || (r.active && (sc > 0x1p20 * r.scale_cur || sc < 0x1p-20 * r.scale_cur))) {
+            r.scale_cur = r.scale_next = sc;
+            again = true;
+        }
     }
-    ir_push_state(pl, run);
-    ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
-    if (keep_x) read_norms(pl, 2 * int(pl.mem.size()));
+    if (again) {
+        ir_push_state(pl, run);
+        ir_residual_norm(pl, m0, m1, keep_x ? 0 : 1);
+        if (keep_x) read_norms(pl, 2 * int(pl.mem.size()));
+    }
     const int M = int(pl.mem.size());
     for (int m = m0; m < m1; ++m) {
         MemberRun &r = *run[m];

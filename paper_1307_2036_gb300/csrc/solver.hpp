@@ -58,6 +58,7 @@ struct DevBuf {
 // Device geometry of one level: column metrics and connectivity (FP64 and FP32).
 struct LevelGeom {
     int n = 0, ncol = 0;
+    double area_sq = 0.0;  // sum of the squared cell areas
     DevBuf area64, tr64, area32, tr32, nbr, pst;
 };
 
@@ -165,6 +166,9 @@ struct Problem {
     std::vector<double> r;
     int nz = 0, P = 1, nlev = 0;
     size_t N = 0;
+    // ||A_P V_k||_2 over the finest unknowns: the norm of the right-hand side
+    // b = A_P V_k f for f = 1 (its magnitude fixes a first refinement scale)
+    double b_unit_norm = 0.0;
     cudaStream_t stream = nullptr;      // the caller's stream: all work is ordered on it
     int device = 0;                     // the device current at creation (owns every buffer)
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs

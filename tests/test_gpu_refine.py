@@ -100,3 +100,26 @@ def test_batch_mixed_modes_equal_alone(torch_mod, oracle_mod):
     for p, x, res, (xa, ra, ia) in zip(ps, xs, out, alone):
         assert np.array_equal(p.host(x), xa)
         assert res.rel_residual == ra and res.iterations == ia
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
+def test_power_of_two_rhs_scales_the_result_exactly(torch_mod, oracle_mod, case, refine):
+    """x(2^k f) = 2^k x(f) bit for bit, with the same V-cycle count and relative
+    residual: the refinement scales are powers of two.  From x = 0 the first
+    scale normalises b for f = 1; for |k| beyond 2^20 of that (k = +-24, +-40)
+    b is formed again with its own scale, and the result is still the same."""
+    torch = torch_mod
+    p = pair(oracle_mod, case, refine=refine)
+    f = torch.tensor(inputs.uniform_pm1(p.og.shape(), member=604), device="cuda")
+    runs = {}
+    for k in (0, 3, -11, 24, -24, 40, -40):
+        x = torch.empty_like(f)
+        st, res = p.sv.solve(f * 2.0 ** k, x, rtol=1e-9, maxit=40)
+        torch.cuda.synchronize()
+        runs[k] = (st, res.iterations, res.rel_residual, x)
+    st0, it0, rel0, x0 = runs[0]
+    for k, (st, it, rel, x) in runs.items():
+        print(f"k {k:+d}: status {st}, {it} V-cycles, residual {rel:.3e}")
+        assert (st, it, rel) == (st0, it0, rel0), k
+        assert torch.equal(x, x0 * 2.0 ** k), k
