@@ -104,6 +104,12 @@ typedef struct {
                        * below 0.1% of the residual, the residual is recomputed in
                        * FP64 and later steps recompute it; 1 recomputed in FP64 at
                        * every step (0) */
+    int line_part;    /* precision 1, the line solves of the small levels (at most
+                       * 9,728 columns, n_z % 16 == 0, n_z <= 256), which wait on the
+                       * elimination chain of a column: 0 one thread eliminates the
+                       * whole column (twisted Thomas, as on the large levels); 1 eight
+                       * warps eliminate eight segments of it at once, joined by a
+                       * tridiagonal system on the seven levels between them (1) */
 } ellsolve_opts;
 
 typedef struct {

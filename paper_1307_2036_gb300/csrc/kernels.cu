@@ -1087,6 +1087,226 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
 }
 
 // ---------------------------------------------------------------------------
+// Partitioned line solve for the small levels: the vertical tridiagonal
+// systems of the line smoother (Sec. 3.2 block Jacobi; Algorithm Thomas)
+// split into segments, so that a column is eliminated by eight warps at once
+// instead of one thread.  A CTA takes 32 columns (lane = column) with the
+// staging of k_smooth_stg; the nz levels form eight ranges of Ls = nz / 8
+// levels, one per warp.  The last level of ranges 0..6 is a separator; the
+// other levels of a range form its segment.  Writing the tridiagonal rows as
+//     -lo_k e_{k-1} + (lo_k + hi_k + X_k) e_k - hi_k e_{k+1} = r_k
+// (lo_k = A g_k, hi_k = A g_{k+1}, X_k = V_k s > 0, the excess), a warp
+// eliminates its segment with the couplings to the two separators moved to
+// the right-hand side.  It obtains the particular solution y, the responses
+// alpha and beta to a unit value at the separator below and above, and
+// z = 1 - alpha - beta, the response to the segment's excess, which it forms
+// directly (every term positive) instead of by that subtraction.  The
+// separators then satisfy a tridiagonal system of seven unknowns per column:
+//     -lo_q alpha_{q-1} e_{q'} + (...) e_q - hi_q beta_{q+1} e_{q''}
+//       = r_q + lo_q y_{q-1} + hi_q y_{q+1},
+// whose excess is X_q + lo_q z_{q-1} + hi_q z_{q+1}, so the same
+// subtraction-free elimination serves it; warp 0 solves it, and every level
+// follows as e = y + alpha e_below + beta e_above.  The column's elimination
+// chain shrinks from nz steps each way to Ls + Ls + 7 + 7.  The pivots of
+// both eliminations use the excess recurrence of pivot2: E_k = X_k + lo_k
+// rho_{k-1}, p_k = E_k + hi_k, rho_k = E_k / p_k, with rho = 1 at a segment's
+// first level (its coupling below is on the right-hand side).
+// ---------------------------------------------------------------------------
+constexpr int kPtW = 8;  // warps of a partitioned CTA: one range of nz / 8 levels each
+
+__host__ __device__ inline size_t part_smem_bytes(int max_nz) {
+    return size_t(max_nz) * kStgF * 4 +     // staged rows
+           size_t(max_nz) * 2 * 32 * 4 +    // off-row neighbours: horizontal, vertical
+           size_t(2 * max_nz + 4) * 4 +     // V_k [nz], g_k [nz + 1] (padded)
+           size_t(kPtW - 1) * 32 * 4;       // the separators' solution
+}
+
+__global__ void __launch_bounds__(32 * kPtW) k_smooth_part(const Lv<float> *__restrict__ L,
+                                                           const Item *__restrict__ items,
+                                                           float rho, int max_nz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *stg = reinterpret_cast<float *>(smem_raw);
+    float *hb = stg + size_t(max_nz) * kStgF;  // [level][lane]
+    float *vb = hb + size_t(max_nz) * 32;       // [level][lane]
+    float *Vs = vb + size_t(max_nz) * 32;       // [nz]
+    float *Gs = Vs + max_nz;                    // [nz + 1]
+    float *es = Gs + max_nz + 4;                // [separator][lane]
+    const Item it = items[blockIdx.x >> 2];
+    const Lv<float> &d = L[it.lv];
+    const int nc = d.ncol, nz = d.nz, n = d.n, Ls = nz / kPtW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0w = it.col0 + 32 * int(blockIdx.x & 3);
+    const int c = c0w + lane;  // every warp's lane l stands for the same column
+    const bool active = c < nc;
+    const bool upd = it.colour == 0 || column_colour(c, n) == it.colour - 1;
+    const bool zero = it.zero != 0;
+    pdl_trigger();
+    const float *__restrict__ u = d.u[it.in];
+    float *__restrict__ un = d.u[it.out];
+    const float *__restrict__ b = d.b;
+    const size_t snc = size_t(nc);
+
+    float A = 1.f, sv = 1.f, t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    int hd = -1, vd = -1, hc = 0, vc = 0;
+    if (active) {
+        const Column<float> k0 = load_column(d, c);
+        A = k0.A;
+        sv = k0.s;
+        t0 = k0.t0;
+        t1 = k0.t1;
+        t2 = k0.t2;
+        t3 = k0.t3;
+        if (!zero) {
+            const int4 nbr = k0.nb;
+            if (nbr.x != c - 1) { hd = 0; hc = nbr.x; }
+            if (nbr.y != c + 1) { hd = 1; hc = nbr.y; }
+            if (nbr.z != c - n) { vd = 2; vc = nbr.z; }
+            if (nbr.w != c + n) { vd = 3; vc = nbr.w; }
+        }
+    }
+    for (int i = tid; i < nz; i += 32 * kPtW) Vs[i] = d.V[i];
+    for (int i = tid; i <= nz; i += 32 * kPtW) Gs[i] = d.g[i];
+    pdl_wait();  // the iterate and right-hand side come from the kernels before
+    // staging, as in k_smooth_stg: chunk r of levels warp, warp + 8, ...
+    for (int r = lane; r < 34; r += 32) {
+        const float *base;
+        int scol, dst;
+        bool use;
+        if (r < 10) { base = u; scol = c0w - 4 + 4 * r; dst = kOwnT + 4 * r; use = !zero; }
+        else if (r < 18) { base = b; scol = c0w + 4 * (r - 10); dst = kBT + 4 * (r - 10); use = true; }
+        else if (r < 26) { base = u; scol = c0w - n + 4 * (r - 18); dst = kJmT + 4 * (r - 18); use = !zero; }
+        else { base = u; scol = c0w + n + 4 * (r - 26); dst = kJpT + 4 * (r - 26); use = !zero; }
+        if (use && scol >= 0 && scol + 4 <= nc)
+            for (int k = warp; k < nz; k += kPtW)
+                cp_async16(stg + k * kStgF + dst, base + k * snc + scol, 16);
+    }
+    if (hd >= 0)
+        for (int k = warp; k < nz; k += kPtW) cp_async(hb + k * 32 + lane, u + k * snc + hc, true);
+    if (vd >= 0)
+        for (int k = warp; k < nz; k += kPtW) cp_async(vb + k * 32 + lane, u + k * snc + vc, true);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const int own = kOwnT + 4 + lane;
+
+    // Per level of the warp's range: the residual r = b - A u (the FP32
+    // stencil of k_smooth_stg), then one elimination step of the segment.
+    // The forward values (c', f' of y, alpha, z) go to the level's slots that
+    // only its own residual read: rows j-1, j+1 and the off-row neighbours.
+    const int ka = warp * Ls;
+    const int kq = warp < kPtW - 1 ? ka + Ls - 1 : nz;  // the separator (none for the last range)
+    auto resid = [&](int k) -> float {
+        const float *lk = stg + k * kStgF;
+        const float bk = lk[kBT + lane];
+        if (zero) return bk;
+        const float u0 = lk[own];
+        const float um = k == 0 ? 0.f : lk[own - kStgF];
+        const float up = k == nz - 1 ? 0.f : lk[own + kStgF];
+        float nw = lk[own - 1], ne = lk[own + 1], ns = lk[kJmT + lane], nn = lk[kJpT + lane];
+        if (hd >= 0 || vd >= 0) {
+            const float vh = hb[k * 32 + lane], vv = vb[k * 32 + lane];
+            nw = hd == 0 ? vh : nw;
+            ne = hd == 1 ? vh : ne;
+            ns = vd == 2 ? vv : ns;
+            nn = vd == 3 ? vv : nn;
+        }
+        float horiz = __fmul_rn(t0, __fsub_rn(u0, nw));
+        horiz = __fmaf_rn(t1, __fsub_rn(u0, ne), horiz);
+        horiz = __fmaf_rn(t2, __fsub_rn(u0, ns), horiz);
+        horiz = __fmaf_rn(t3, __fsub_rn(u0, nn), horiz);
+        float vert = __fmul_rn(Gs[k + 1], __fsub_rn(u0, up));
+        vert = __fmaf_rn(Gs[k], __fsub_rn(u0, um), vert);
+        const float Vk = Vs[k];
+        float Au = __fmul_rn(A, __fmul_rn(Vk, u0));
+        Au = __fmaf_rn(Vk, horiz, Au);
+        Au = __fmaf_rn(A, vert, Au);
+        return __fsub_rn(bk, Au);
+    };
+    {
+        float ratio = 1.f, py = 0.f, pa = 1.f, pz = 0.f;
+#pragma unroll 2
+        for (int k = ka; k < kq; ++k) {
+            const float r = resid(k);
+            const float lo = __fmul_rn(A, Gs[k]), hi = __fmul_rn(A, Gs[k + 1]);
+            const float X = __fmul_rn(Vs[k], sv);
+            const float E = __fmaf_rn(lo, ratio, X);
+            const float inv = rcp(__fadd_rn(E, hi));
+            ratio = __fmul_rn(E, inv);
+            py = __fmul_rn(__fmaf_rn(lo, py, r), inv);
+            pa = __fmul_rn(__fmul_rn(lo, pa), inv);
+            pz = __fmul_rn(__fmaf_rn(lo, pz, X), inv);
+            float *lk = stg + k * kStgF;
+            lk[kJmT + lane] = __fmul_rn(hi, inv);  // c'
+            lk[kJpT + lane] = py;
+            hb[k * 32 + lane] = pa;
+            vb[k * 32 + lane] = pz;
+        }
+        if (kq < nz) stg[kq * kStgF + kBT + lane] = resid(kq);  // the separator's residual
+        // back substitution: y, alpha, beta, z in place of c', f'y, f'alpha, f'z
+        float y = 0.f, al = 0.f, be = 1.f, z = 0.f;
+#pragma unroll 2
+        for (int k = kq - 1; k >= ka; --k) {
+            float *lk = stg + k * kStgF;
+            const float cp = lk[kJmT + lane];
+            y = __fmaf_rn(cp, y, lk[kJpT + lane]);
+            al = __fmaf_rn(cp, al, hb[k * 32 + lane]);
+            z = __fmaf_rn(cp, z, vb[k * 32 + lane]);
+            be = __fmul_rn(cp, be);
+            lk[kJmT + lane] = be;
+            lk[kJpT + lane] = y;
+            hb[k * 32 + lane] = al;
+            vb[k * 32 + lane] = z;
+        }
+    }
+    __syncthreads();
+    // the separators' system (seven unknowns per column), by warp 0
+    if (warp == 0) {
+        float cq[kPtW - 1], fq[kPtW - 1];
+        float ratio = 0.f, fp = 0.f;
+#pragma unroll
+        for (int w = 0; w < kPtW - 1; ++w) {
+            const int q = (w + 1) * Ls - 1;
+            const float *lq = stg + q * kStgF, *lb = lq - kStgF, *la = lq + kStgF;
+            const float lo_q = __fmul_rn(A, Gs[q]), hi_q = __fmul_rn(A, Gs[q + 1]);
+            const float lo = __fmul_rn(lo_q, hb[(q - 1) * 32 + lane]);  // alpha below
+            const float hi = __fmul_rn(hi_q, la[kJmT + lane]);          // beta above
+            float X = __fmul_rn(Vs[q], sv);
+            X = __fmaf_rn(lo_q, vb[(q - 1) * 32 + lane], X);
+            X = __fmaf_rn(hi_q, vb[(q + 1) * 32 + lane], X);
+            float r = lq[kBT + lane];
+            r = __fmaf_rn(lo_q, lb[kJpT + lane], r);
+            r = __fmaf_rn(hi_q, la[kJpT + lane], r);
+            const float E = __fmaf_rn(lo, ratio, X);
+            const float inv = rcp(__fadd_rn(E, hi));
+            ratio = __fmul_rn(E, inv);
+            cq[w] = __fmul_rn(hi, inv);
+            fp = __fmul_rn(__fmaf_rn(lo, fp, r), inv);
+            fq[w] = fp;
+        }
+        float e = 0.f;
+#pragma unroll
+        for (int w = kPtW - 2; w >= 0; --w) {
+            e = __fmaf_rn(cq[w], e, fq[w]);
+            es[w * 32 + lane] = e;
+        }
+    }
+    __syncthreads();
+    // every level of the range: e = y + alpha e_below + beta e_above; u += rho e
+    const float eb = warp > 0 ? es[(warp - 1) * 32 + lane] : 0.f;
+    const float ea = warp < kPtW - 1 ? es[warp * 32 + lane] : 0.f;
+    const int ke = warp < kPtW - 1 ? kq + 1 : nz;
+    for (int k = ka; k < ke; ++k) {
+        const float *lk = stg + k * kStgF;
+        float e;
+        if (k == kq) e = ea;
+        else e = __fmaf_rn(lk[kJmT + lane], ea, __fmaf_rn(hb[k * 32 + lane], eb, lk[kJpT + lane]));
+        const float uo = zero ? 0.f : lk[own];
+        const float u1 = __fmaf_rn(rho, e, uo);
+        if (active) __stcs(un + size_t(k) * snc + c, upd ? u1 : uo);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Residual / apply (Sec. 3.1 stencil).
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
@@ -2424,6 +2644,10 @@ cudaError_t launch_smooth_tw(cudaStream_t s, const Lv<float> *L, const Item *ite
     return launch_tw_zf<0, 4>(s, L, items, nitems, rho, max_nz, ctas_per_sm, aligned, tmem);
 }
 
+bool smooth_part_fits(int max_nz) {
+    return max_nz % 16 == 0 && max_nz <= 256 && part_smem_bytes(max_nz) <= kSmemCap;
+}
+
 bool smooth_stg_fits(int max_nz) {
     return max_nz % 16 == 0 && max_nz <= kTwTmemMaxNz && stg_smem_bytes(max_nz) <= kSmemCap;
 }
@@ -2448,6 +2672,16 @@ cudaError_t launch_smooth_stg(cudaStream_t s, const Lv<float> *L, const Item *it
     if (nitems <= 0) return cudaSuccess;
     if (zero_mode == 1) return launch_stg_z<1>(s, L, items, nitems, rho, max_nz);
     return launch_stg_z<0>(s, L, items, nitems, rho, max_nz);
+}
+
+cudaError_t launch_smooth_part(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                               float rho, int max_nz) {
+    if (nitems <= 0) return cudaSuccess;
+    const size_t bytes = part_smem_bytes(max_nz);
+    cudaError_t e = set_smem(k_smooth_part, bytes);
+    if (e != cudaSuccess) return e;
+    return launch_k(true, k_smooth_part, dim3(unsigned(nitems) * 4u), dim3(32 * kPtW), bytes, s, L,
+                    items, rho, max_nz);
 }
 
 bool smooth_tw_fits(int max_nz, int ring) {

@@ -36,6 +36,15 @@ cudaError_t launch_smooth_stg(cudaStream_t s, const Lv<float> *L, const Item *it
                               float rho, int max_nz, int zero_mode);
 bool smooth_stg_fits(int max_nz);
 
+// The line sweep of small levels with each column's tridiagonal solve split
+// into eight segments joined by a system on the seven levels between them
+// (one CTA of eight warps per 32 columns, staged as launch_smooth_stg).  The
+// same solve up to rounding, not the same bits; zero flags per item.  Valid
+// where smooth_part_fits(max_nz) (n_z % 16 == 0, n_z <= 256).
+cudaError_t launch_smooth_part(cudaStream_t s, const Lv<float> *L, const Item *items, int nitems,
+                               float rho, int max_nz);
+bool smooth_part_fits(int max_nz);
+
 // Whether the generic smoother keeps its Thomas coefficients in the level's
 // aux buffer (true) or in shared memory, for a largest nz of max_nz.
 bool smooth_uses_global_scratch(int max_nz, size_t elem_bytes);

@@ -443,11 +443,13 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
     auto lvl_count = [&](int m) { return mem[m]->nlev; };
 
     auto rows_level = [&](int m, int l) { return precision == 1 && rows_eligible(*mem[m], l); };
+    auto part_level = [&](int m, int l) { return precision == 1 && part_eligible(*mem[m], l); };
     auto emit_smooth_one = [&](const std::vector<std::pair<int, int>> &ml, double rho,
-                               int colour) {
+                               int colour, bool part) {
         if (ml.empty()) return;
         Op op;
         op.kind = Op::kSmooth;
+        op.part = part;
         op.off = int(items.size());
         op.rho = rho;
         op.max_nz = 0;
@@ -473,14 +475,12 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
         }
         op.n = int(items.size()) - op.off;
         op.zero_mode = z_items == 0 ? 0 : (nz_items == 0 ? 1 : 2);
-        if (op.zero_mode == 2) op.rows_ok = false;
+        if (op.zero_mode == 2 && !op.part) op.rows_ok = false;  // the partitioned kernel reads each item's flag
         prog.ops.push_back(op);
     };
-    // one launch for the levels the row-staged kernel takes, one for the rest,
-    // so that a member's kernel does not depend on the other members
-    // One sweep: a launch for the levels the row-staged kernel takes and one
-    // for the rest, so that a member's kernel does not depend on the other
-    // members; members with the block red-black SOR smoother take two
+    // One sweep: a launch for the levels that take the partitioned line solve,
+    // one for the levels the row-staged kernel takes and one for the rest, so
+    // that a member's kernel does not depend on the other members; members with the block red-black SOR smoother take two
     // half-sweeps (red, then black).
     // Members are grouped by (smoother, damping): each member sweeps with its
     // own relaxation parameter (the coarsest level undamped, rho = 1).
@@ -500,10 +500,15 @@ const Program &Plan::program(bool fine_zero, const std::vector<int> &fine_cur) {
             const int passes = key.first == 1 ? 2 : 1;
             for (int pass = 0; pass < passes; ++pass) {
                 const int colour = key.first == 1 ? pass + 1 : 0;
-                std::vector<std::pair<int, int>> a, b;
-                for (auto ml1 : group) (rows_level(ml1.first, ml1.second) ? a : b).push_back(ml1);
-                emit_smooth_one(a, key.second, colour);
-                emit_smooth_one(b, key.second, colour);
+                std::vector<std::pair<int, int>> pt, a, b;
+                for (auto ml1 : group)
+                    (part_level(ml1.first, ml1.second)   ? pt
+                     : rows_level(ml1.first, ml1.second) ? a
+                                                         : b)
+                        .push_back(ml1);
+                emit_smooth_one(pt, key.second, colour, true);
+                emit_smooth_one(a, key.second, colour, false);
+                emit_smooth_one(b, key.second, colour, false);
             }
         }
     };
@@ -672,11 +677,26 @@ bool rows_eligible(const Problem &p, int level) {
     return p.nz % 16 == 0 && smooth_tw_fits(p.nz, 8);
 }
 
+// Levels whose partitioned sweep fits one wave (two CTAs of 32 columns per
+// SM): their sweeps wait on the elimination chain of a column, which the
+// partitioned solve cuts.  On larger levels (6 x 64 x 64 and up) the
+// streaming ring kernel is faster (C3 level 3: 24 against 30 us per sweep).
+constexpr int kPartMaxCols = 2 * 152 * 32;
+
+bool part_eligible(const Problem &p, int level) {
+    return p.opts.precision == 1 && p.opts.line_part == 1 && rows_eligible(p, level) &&
+           smooth_part_fits(p.nz) && p.lev[level].ncol <= kPartMaxCols;
+}
+
 template <typename T>
-void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
-                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned,
-                     int level) {
-    if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
+static void launch_smoother_op(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it,
+                               int n, double rho, int max_nz, int zero_mode, bool rows_ok,
+                               bool aligned, int level, bool part) {
+    if (sizeof(T) == 4 && part) {
+        check_cuda(launch_smooth_part(s, reinterpret_cast<const Lv<float> *>(L), it, n,
+                                      float(rho), max_nz),
+                   "smooth_part");
+    } else if (sizeof(T) == 4 && rows_ok && zero_mode != 2) {
         const Lv<float> *Lf = reinterpret_cast<const Lv<float> *>(L);
         const LevelShape &sh = p.level_shape(level);
         const bool stg = smooth_stg_fits(max_nz) && (sh.staged == 1 || (sh.staged == 0 && n < 152));
@@ -690,6 +710,14 @@ void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Ite
     } else {
         check_cuda(launch_smooth<T>(s, L, it, n, T(rho), max_nz, zero_mode), "smooth");
     }
+}
+
+template <typename T>
+void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
+                     double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned,
+                     int level) {
+    launch_smoother_op<T>(p, s, L, it, n, rho, max_nz, zero_mode, rows_ok, aligned, level,
+                          sizeof(T) == 4 && rows_ok && part_eligible(p, level));
 }
 template void launch_smoother<float>(const Problem &, cudaStream_t, const Lv<float> *,
                                      const Item *, int, double, int, int, bool, bool, int);
@@ -718,8 +746,8 @@ static void run_program(Plan &pl, const Program &prog) {
             case Op::kSmooth: {
                 const bool timed = p0.prof && op.finest;
                 if (timed) p0.prof_mark_begin(s);
-                launch_smoother<T>(p0, s, L, it + op.off, op.n, op.rho, op.max_nz, op.zero_mode,
-                                   op.rows_ok, op.aligned, op.tune);
+                launch_smoother_op<T>(p0, s, L, it + op.off, op.n, op.rho, op.max_nz, op.zero_mode,
+                                      op.rows_ok, op.aligned, op.tune, op.part);
                 if (timed) p0.prof_mark_end(s, op.bytes);
                 count(pl);
                 break;
@@ -1607,6 +1635,7 @@ void ellsolve_default_opts(ellsolve_opts *o) {
     o->precond = 0;
     o->fmg = 0;
     o->refine = 0;
+    o->line_part = 1;
 }
 
 const char *ellsolve_last_error(void) { return t_last_error.c_str(); }
@@ -1876,7 +1905,7 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
             LevelShape &sh = h->shape[size_t(l)];
             // (a) the line smoother: resident CTAs per SM, ring depth and where
             // f' is parked, on the levels the twisted kernel takes
-            if (rows_eligible(*h, l)) {
+            if (rows_eligible(*h, l) && !part_eligible(*h, l)) {
                 std::vector<LevelShape> cand;  // (ctas, ring, tmem, staged)
                 const bool tm_ok = h->nz <= 256;
                 const bool stg_ok = smooth_stg_fits(h->nz);
@@ -1913,6 +1942,12 @@ ellsolve_status ellsolve_autotune(ellsolve_t h, int *out_ctas, double *out_ms) {
                 sh.tmem = keep.tmem;
                 sh.staged = keep.staged;
                 if (l == 0) ms0 = best;
+            } else if (l == 0 && part_eligible(*h, l)) {
+                // the partitioned line solve has no launch shape: its time only
+                ms0 = time_ms(s, e0, e1, [&] {
+                    launch_smoother<float>(*h, s, dd.as<Lv<float>>(), di.as<Item>(), nitems, 0.8,
+                                           h->nz, 0, true, Ls.n % 32 == 0, l);
+                });
             }
             // (b) the transfers of small levels: how far to split them along
             // the vertical (the row-staged restriction of large levels is not

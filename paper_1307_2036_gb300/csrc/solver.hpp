@@ -109,6 +109,7 @@ struct Op {
     int zero_mode = 0;        // smoother items: 0 none / 1 all start from zero, 2 mixed
     bool rows_ok = false;     // every level in the op suits the row-staged FP32 smoother
     bool aligned = false;     // every level in the op has n % 32 == 0
+    bool part = false;        // every level in the op takes the partitioned line solve
     int tune = 0;             // level whose launch shape the op takes (its first item's)
     int member = 0, level = 0, buf = 0;  // kMemset target
 };
@@ -242,12 +243,15 @@ bool ir_zero_unwritten(Plan &pl, const std::vector<MemberRun *> &run);
 ellsolve_status run_result(const MemberRun &r, double secs, ellsolve_result *res);
 
 // One line-smoother launch: the twisted FP32 kernel where `rows_ok`, else the
-// generic kernel; `level`: whose launch shape to take.
+// generic kernel; `level`: whose launch shape to take.  The items are one
+// member's level, which takes the partitioned line solve where part_eligible.
 template <typename T>
 void launch_smoother(const Problem &p, cudaStream_t s, const Lv<T> *L, const Item *it, int n,
                      double rho, int max_nz, int zero_mode, bool rows_ok, bool aligned,
                      int level);
 bool rows_eligible(const Problem &p, int level);
+// FP32 level whose line solves are partitioned (opts.line_part, small levels)
+bool part_eligible(const Problem &p, int level);
 bool restrict_rows_eligible(const Problem &p, int level);
 bool restrict_rows_preferred(const Problem &p, int level);
 

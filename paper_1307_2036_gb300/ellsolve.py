@@ -37,7 +37,8 @@ class ellsolve_opts(C.Structure):
                 ("nu_post", C.c_int), ("nu_coarse", C.c_int), ("damping", C.c_double),
                 ("coarsest_min", C.c_int), ("max_levels", C.c_int), ("prolong", C.c_int),
                 ("inner_cycles", C.c_int), ("use_graph", C.c_int), ("smoother", C.c_int),
-                ("precond", C.c_int), ("fmg", C.c_int), ("refine", C.c_int)]
+                ("precond", C.c_int), ("fmg", C.c_int), ("refine", C.c_int),
+                ("line_part", C.c_int)]
 
 
 class ellsolve_result(C.Structure):

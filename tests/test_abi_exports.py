@@ -49,3 +49,17 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     st = ellsolve.ellsolve_create(ctypes.byref(g), 0.01, 1.0, r, None, None, ctypes.byref(h))
     assert st == ellsolve.ERR_ARG and not h.value
     assert b"increasing" in ellsolve.ellsolve_last_error()
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of ellsolve_grid, ellsolve_opts and ellsolve_result
+    list the header's fields in the header's order."""
+    import re
+    from paper_1307_2036_gb300 import ellsolve
+    text = open(os.path.join(ROOT, "include", "ellsolve.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    structs = {m.group(2): m.group(1)
+               for m in re.finditer(r"typedef struct \{([^{}]*)\}\s*(\w+);", text)}
+    for name in ("ellsolve_grid", "ellsolve_opts", "ellsolve_result"):
+        fields = re.findall(r"\b(?:int|double)\s+(\w+);", structs[name])
+        assert [f for f, _ in getattr(ellsolve, name)._fields_] == fields, name

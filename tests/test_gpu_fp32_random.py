@@ -138,3 +138,54 @@ def test_fp32_smoother_random_iterate(torch_mod, oracle_mod, case):
     print(f"{n}x{n}x{nz} smoother {smoother}: componentwise backward error {worst:.2f} eps32 "
           f"(bar {C_BACKWARD:.0f}), forward error of two sweeps against the oracle {fwd:.2e}")
     assert worst <= C_BACKWARD
+
+
+# Levels of at most 9,728 columns take the partitioned line solve (eight
+# segments per column joined by a system on the seven levels between them):
+# the same backward-error bar, and the whole-column elimination
+# (line_part = 0) beside it for reference.
+PART_CASES = [
+    (1, 32, 128, True, 0.01, 1.0, 0),    # 6144 columns, n % 32 == 0
+    (1, 40, 64, True, 0.01, 1.0, 0),     # 9600 columns, n % 32 != 0 (neighbour buffer)
+    (1, 32, 128, True, 0.01, 1.0, 1),    # block red-black SOR half-sweeps
+    (0, 96, 128, True, 0.1, 25.0, 0),    # box, strong vertical coupling
+    (1, 16, 256, True, 0.01, 1.0, 0),    # n_z = 256: segments of 31 levels
+    (0, 8, 16, False, 0.01, 1.0, 0),     # n_z = 16: segments of one level
+]
+PART_IDS = ["sph32z128", "sph40z64", "sph32z128rb", "box96z128strong", "sph16z256", "box8z16"]
+
+
+@pytest.mark.parametrize("case", PART_CASES, ids=PART_IDS)
+def test_fp32_partitioned_smoother_random_iterate(torch_mod, oracle_mod, case):
+    kind, n, nz, graded, w2, l2, smoother = case
+    worst = {}
+    for line_part in (1, 0):
+        p = Pair(oracle_mod, kind, n, nz, omega2=w2, lambda2=l2, graded=graded, precision=1,
+                 smoother=smoother, line_part=line_part)
+        nc = p.og.ncol()
+        assert nc <= 9728
+        pc = Pieces(p.og)
+        sh = p.og.shape()
+        u0 = f32exact(inputs.uniform_pm1(sh, member=511)).reshape(nz, nc)
+        b = f32exact(p.og.volumes() * inputs.uniform_pm1(sh, member=512)).reshape(nz, nc)
+        rho = 1.0 if smoother == 1 else 0.8
+        bd = p.dev(b.reshape(sh), True)
+        ud = p.dev(u0.reshape(sh), True)
+        iters = [u0]
+        for sweep in range(2):
+            p.sv.level_smooth(0, bd, ud, nsweeps=1, rho=rho, fp32=True)
+            iters.append(p.host(ud).reshape(nz, nc))
+        w = 0.0
+        for s in range(2):
+            ua, ub = iters[s], iters[s + 1]
+            if smoother == 0:
+                w = max(w, backward_error(pc, b, ua, ub, rho))
+            else:
+                red = p.og.colour() == 0
+                mid = np.where(red[None, :], ub, ua)
+                w = max(w, backward_error(pc, b, ua, mid, rho, cols=red))
+                w = max(w, backward_error(pc, b, mid, ub, rho, cols=~red))
+        worst[line_part] = w
+    print(f"{n}x{n}x{nz} smoother {smoother}: componentwise backward error, partitioned "
+          f"{worst[1]:.2f} eps32, whole column {worst[0]:.2f} eps32 (bar {C_BACKWARD:.0f})")
+    assert worst[1] <= C_BACKWARD and worst[0] <= C_BACKWARD
