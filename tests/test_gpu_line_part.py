@@ -13,9 +13,10 @@ from gpu_util import Pair, rel_l2, require_gpu
 pytestmark = pytest.mark.gpu
 
 # kind, n, nz, graded, omega2, lambda2, smoother
-CASES = [(1, 64, 128, True, 0.01, 1.0, 0), (0, 96, 64, True, 0.1, 25.0, 0),
-         (1, 32, 256, True, 0.05, 4.0, 1), (1, 24, 16, False, 0.01, 1.0, 0)]
-IDS = ["sph64z128", "box96z64strong", "sph32z256rb", "sph24z16"]
+# (sizes that the oracle's FP64 multigrid solves to 1e-12 in seconds)
+CASES = [(1, 24, 128, True, 0.01, 1.0, 0), (0, 64, 64, True, 0.1, 25.0, 0),
+         (1, 16, 256, True, 0.05, 4.0, 1), (1, 24, 16, False, 0.01, 1.0, 0)]
+IDS = ["sph24z128", "box64z64strong", "sph16z256rb", "sph24z16"]
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +35,7 @@ def test_partitioned_and_whole_column_solves_agree(torch_mod, oracle_mod, case):
         x = p.empty()
         st, res = p.sv.solve(p.dev(f), x, rtol=1e-10, maxit=60)
         out[line_part] = (st, res.iterations, p.host(x))
-    u_ref = p.og.mg_solve(p.og.volumes() * f, rtol=1e-13, maxit=200)[0]
+    u_ref = p.og.mg_solve(p.og.volumes() * f, rtol=1e-12, maxit=100)[0]
     e1, e0 = rel_l2(out[1][2], u_ref), rel_l2(out[0][2], u_ref)
     print(f"{(kind, n, nz, smoother)}: partitioned {out[1][1]} V-cycles (error {e1:.2e}), "
           f"whole column {out[0][1]} (error {e0:.2e})")
