@@ -1088,9 +1088,9 @@ __global__ void __launch_bounds__(32 * kStgW) k_smooth_stg(const Lv<float> *__re
 
 // ---------------------------------------------------------------------------
 // Partitioned line solve for the small levels: the vertical tridiagonal
-// systems of the line smoother (Sec. 3.2 block Jacobi; Algorithm Thomas)
-// split into segments, so that a column is eliminated by eight warps at once
-// instead of one thread.  A CTA takes 32 columns (lane = column) with the
+// systems of the line smoother (Sec. 4.2; the block Jacobi of Sec. 3.2;
+// Algorithm Thomas) split into segments, so that a column is eliminated by
+// eight warps at once instead of one thread.  A CTA takes 32 columns (lane = column) with the
 // staging of k_smooth_stg; the nz levels form eight ranges of Ls = nz / 8
 // levels, one per warp.  The last level of ranges 0..6 is a separator; the
 // other levels of a range form its segment.  Writing the tridiagonal rows as
